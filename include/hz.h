@@ -1,0 +1,177 @@
+/*
+ * hz.h — C ABI of the GB300 two-level ORAS / FGMRES Helmholtz solver.
+ *
+ * The library solves the Galerkin P3 discretisation (Lagrange elements of
+ * order 3 on a tetrahedral mesh) of the acoustic Helmholtz equation,
+ * Sec. "Tetrahedral finite element method", Eq. eqh and Eq. eq1:
+ *
+ *     -Lap u - k^2 u = s  in Omega,   k = omega / c(x),  omega = 2 pi f,
+ *     d_n u - i k u = g   on absorbing (Robin) faces,
+ *     u = 0               on Dirichlet (free-surface) faces,
+ *
+ * (time convention e^{-i omega t}; a unit point source radiates like
+ * e^{ikr} / (4 pi r)), i.e. the complex-symmetric sparse system
+ *     A = sum_e (K_e - omega^2 m_e M_e) - i omega sum_{Robin f} sqrt(m_e) B_f,
+ * m_e = 1 / c_e^2, by flexible GMRES (Sec. "Domain decomposition
+ * preconditioner") preconditioned by the two-level method of Eq. 2lvl,
+ *     M^{-1} = M1^{-1} (I - A Q) + Q,  Q = Z E^{-1} Z^T,  E = Z^T A Z,
+ * with the one-level optimized restricted additive Schwarz operator of
+ * Eq. oras, M1^{-1} = sum_i R_i^T D_i A_i^{-1} R_i, whose local matrices A_i
+ * carry absorbing conditions on the subdomain interfaces. The coarse problem
+ * is solved by a fixed number of GMRES iterations preconditioned by one-level
+ * ORAS on the coarse mesh (10 in the paper).
+ *
+ * Conventions for every call:
+ *   - Units: metres, m/s, Hz. Complex numbers are interleaved (re, im)
+ *     doubles, the layout of a C99 double complex / torch.complex128.
+ *   - Blocks of right-hand sides and wavefields are source-major:
+ *     [ns][n][2] doubles (each source's n complex values contiguous).
+ *   - Dof numbering is the library's own; hz_dof_coords gives the node
+ *     coordinates so that callers can match dofs by position.
+ *   - Input arrays are read during the call and stay owned by the caller;
+ *     output arrays are caller-allocated. A context owns all the device
+ *     memory it allocates until hz_free.
+ *   - Work is issued on the CUDA stream given to hz_setup. A context is not
+ *     thread-safe; one call at a time per context.
+ *   - Every int-returning call returns HZ_OK (0) or an HZ_E* code and never
+ *     aborts; hz_last_error() gives a one-line description of the last error
+ *     on the calling thread.
+ */
+#ifndef HZ_H
+#define HZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  HZ_OK = 0,
+  HZ_EINVAL = 1,      /* bad mesh, partition, size or option */
+  HZ_ENOMEM = 2,      /* device or host allocation failed */
+  HZ_ECUDA = 3,       /* a CUDA runtime call failed */
+  HZ_EINTERNAL = 4,   /* inconsistent internal state (a bug) */
+  HZ_ESINGULAR = 5,   /* zero pivot with perturbation disabled (pivot_tau = 0) */
+  HZ_ENOTCONV = 6,    /* maxit reached; outputs hold the last iterate */
+  HZ_EBREAKDOWN = 7   /* Krylov breakdown that left a column unconverged */
+};
+
+enum { HZ_BC_ROBIN = 0, HZ_BC_DIRICHLET = 1 };
+enum { HZ_COARSE_NONE = 0, HZ_COARSE_GMRES = 1, HZ_COARSE_DIRECT = 2 };
+enum { HZ_PREC_FP64 = 0, HZ_PREC_MIXED = 1 };
+
+typedef struct hz_ctx hz_ctx; /* opaque */
+
+/* Tetrahedral mesh. Boundary faces not listed in bfaces get the natural
+ * (homogeneous Neumann) condition; a listed face must be exterior. */
+typedef struct hz_mesh {
+  const double* xyz;        /* [nv][3] vertex coordinates, metres */
+  int64_t nv;
+  const int32_t* tets;      /* [ne][4] vertex ids in [0, nv) */
+  int64_t ne;
+  const int32_t* bfaces;    /* [nbf][3] vertex ids of exterior triangles */
+  const int32_t* bface_tag; /* [nbf] HZ_BC_ROBIN (absorbing) or HZ_BC_DIRICHLET (free surface) */
+  int64_t nbf;
+} hz_mesh;
+
+typedef struct hz_options {
+  int32_t precision;        /* HZ_PREC_FP64 (default) or HZ_PREC_MIXED */
+  double rtol;              /* FGMRES stop: ||b - A u|| / ||b|| <= rtol per column (1e-6) */
+  int32_t maxit;            /* maximum FGMRES iterations (500) */
+  int32_t restart;          /* FGMRES restart length m (30) */
+  int32_t max_block;        /* maximum right-hand sides per block (64) */
+  int32_t coarse_mode;      /* HZ_COARSE_GMRES (default), HZ_COARSE_NONE, HZ_COARSE_DIRECT */
+  int32_t coarse_inner_its; /* inner coarse GMRES iterations (10) */
+  int32_t leaf_size;        /* nested-dissection leaf size (64) */
+  double pivot_tau;         /* static pivot perturbation, relative to max|A_i| (1e-12) */
+  int32_t verbose;          /* 0 silent */
+} hz_options;
+
+typedef struct hz_stats {
+  int32_t iterations;       /* FGMRES iterations of the last solve (max over columns) */
+  int32_t restarts;
+  int32_t converged;        /* 1 if every column reached rtol (true residual) */
+  int32_t ncols;
+  double max_rel_residual;  /* max over columns of ||b - A u|| / ||b|| (true residual) */
+  double solve_seconds;     /* wall time of the solve call */
+  double setup_seconds;     /* wall time of hz_setup (host + device) */
+  double factor_seconds;    /* device factorisation time inside hz_setup */
+} hz_stats;
+
+typedef struct hz_info {
+  int64_t n;                /* global dofs */
+  int64_t nnz;              /* nonzeros of A */
+  int64_t nnz_imag;         /* entries of A with a nonzero imaginary part (Robin faces) */
+  int32_t nparts;
+  int64_t sub_rows;         /* sum of overlapping subdomain sizes n_i */
+  int64_t n_coarse;         /* coarse dofs (0 without coarse level) */
+  int64_t nnz_coarse;       /* nonzeros of E */
+  int64_t factor_entries;   /* stored factor entries, fine level: sum_t k_t (k_t + 1)/2 + k_t m_t */
+  int64_t coarse_factor_entries;
+  int64_t front_entries;    /* sum_t f_t^2 (device front storage, fine level) */
+  int32_t max_front;        /* largest front order f_t (fine) */
+  int32_t nfronts;
+  int32_t nlevels;          /* tree heights (fine) */
+  int32_t perturbed_pivots; /* static perturbations applied in the factorisations */
+  double device_bytes;      /* device memory held by the context */
+} hz_info;
+
+/* Fills *opt with the defaults listed above. */
+int hz_default_options(hz_options* opt);
+
+/* Set up a solver for one mesh and frequency (Sec. "Domain decomposition
+ * preconditioner"): P3 numbering, assembly of A, the overlapping subdomains
+ * of the element partition (overlap: elements sharing a vertex), local Robin
+ * matrices A_i, the coarse space on `coarse` (a mesh nested in `fine`, or
+ * NULL for coarse_mode = HZ_COARSE_NONE), nested-dissection symbolic
+ * analysis on the host and the batched multifrontal factorisation of every
+ * A_i (and E_i / E) on the device.
+ *   velocity  [ne] per-element wavespeed c_e > 0 (m/s)
+ *   elem_part [ne] subdomain of each element, in [0, nparts); every part
+ *             non-empty
+ *   stream    cudaStream_t (NULL: the legacy default stream)
+ * Errors: HZ_EINVAL (bad input), HZ_ENOMEM, HZ_ECUDA. *out is NULL on error. */
+int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const int32_t* elem_part,
+             int32_t nparts, const hz_mesh* coarse, const hz_options* opt, void* stream, hz_ctx** out);
+
+int hz_ndof(const hz_ctx* ctx, int64_t* n);
+/* Coordinates [n][3] of the P3 nodes in the library's dof order (host). */
+int hz_dof_coords(const hz_ctx* ctx, double* xyz);
+int hz_get_info(const hz_ctx* ctx, hz_info* info);
+
+/* Wavefields for point sources (Sec. "Numerical results": a point source in
+ * the subsurface): right-hand side F_j = a phi_j(x_s) in the lowest-index
+ * element containing x_s, zero on Dirichlet dofs.
+ *   src_xyz [ns][3], src_amp [ns][2] complex amplitudes
+ *   u       [ns][n][2] output, host (u_on_device = 0) or device pointer
+ *   stats   may be NULL
+ * Blocks of up to max_block sources are solved together (one Krylov space
+ * per source). Returns HZ_ENOTCONV when maxit is reached first (u then holds
+ * the last iterate). */
+int hz_solve(hz_ctx* ctx, const double* src_xyz, const double* src_amp, int32_t ns, double* u,
+             int32_t u_on_device, hz_stats* stats);
+
+/* Same for given right-hand sides F [ns][n][2] (host or device). */
+int hz_solve_rhs(hz_ctx* ctx, const double* F, int32_t ns, int32_t F_on_device, double* u, int32_t u_on_device,
+                 hz_stats* stats);
+
+/* Y = A X, X and Y [s][n][2], host or device (both on the same side). */
+int hz_apply_A(hz_ctx* ctx, const double* X, double* Y, int32_t s, int32_t on_device);
+
+/* Y = M^{-1} X (Eq. 2lvl with the configured coarse mode; Eq. oras alone
+ * with HZ_COARSE_NONE), X and Y [s][n][2]. */
+int hz_apply_prec(hz_ctx* ctx, const double* X, double* Y, int32_t s, int32_t on_device);
+
+/* Host copy of A in CSR form: rowptr [n+1], col [nnz], val [nnz][2]. */
+int hz_matrix_csr(const hz_ctx* ctx, int64_t* rowptr, int32_t* col, double* val);
+
+void hz_free(hz_ctx* ctx);
+const char* hz_strerror(int code);
+const char* hz_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HZ_H */

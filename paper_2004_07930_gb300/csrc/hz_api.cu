@@ -1,0 +1,862 @@
+// C ABI: setup (host assembly, subdomains, symbolic; device factorisation)
+// and the flexible GMRES solve driven by the device kernels.
+//
+// Sec. "Domain decomposition preconditioner": GMRES on A u = b with the
+// two-level preconditioner of Eq. 2lvl; the coarse problem solved by a fixed
+// number of GMRES iterations preconditioned by one-level ORAS on the coarse
+// mesh. GMRES is run right-preconditioned and flexible (the inner coarse
+// iteration makes M^{-1} vary between applications), one Krylov space per
+// right-hand side, so the monitored residual is the paper's
+// ||A u - b|| / ||b|| (Sec. "Tetrahedral finite element method").
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <string>
+
+#include "../../include/hz.h"
+#include "dd_host.h"
+#include "kernels.cuh"
+
+using namespace hz;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct CudaFail {
+  cudaError_t e;
+  const char* what;
+};
+
+#define CK(x)                                     \
+  do {                                            \
+    cudaError_t _e = (x);                         \
+    if (_e != cudaSuccess) throw CudaFail{_e, #x}; \
+  } while (0)
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Device allocation tracker: every buffer of a context is released in hz_free.
+struct DevPool {
+  std::vector<void*> ptrs;
+  double bytes = 0;
+  template <typename T>
+  T* alloc(size_t count) {
+    if (count == 0) count = 1;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw HzError{HZ_ENOMEM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed"};
+    }
+    ptrs.push_back(p);
+    bytes += count * sizeof(T);
+    return (T*)p;
+  }
+  template <typename T>
+  T* upload(const std::vector<T>& v, cudaStream_t st) {
+    T* p = alloc<T>(v.size());
+    if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    return p;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+    bytes = 0;
+  }
+};
+
+struct MFHost {
+  int64_t factor_entries = 0, front_entries = 0;
+  int max_front = 0, nfronts = 0, nlevels = 0;
+  std::vector<int> level_ptr;
+};
+
+// Pack the fronts of several local matrices into one device structure;
+// sub_off[i] is the first row of subdomain i in the flat sub-vector.
+void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const FrontTree*>& trees,
+              const std::vector<int64_t>& sub_off, DevMF& mf, MFHost& info, DevPool& pool, cudaStream_t st) {
+  const size_t ns = mats.size();
+  std::vector<int> base(ns + 1, 0);
+  for (size_t i = 0; i < ns; ++i) base[i + 1] = base[i] + (int)trees[i]->k.size();
+  const int nf = base[ns];
+  std::vector<int> k(nf), f(nf), height(nf), child_ptr(nf + 1, 0), child_idx;
+  std::vector<int64_t> Foff(nf + 1, 0), rowoff(nf + 1, 0);
+  for (size_t i = 0; i < ns; ++i) {
+    const FrontTree& T = *trees[i];
+    for (size_t t = 0; t < T.k.size(); ++t) {
+      int g = base[i] + (int)t;
+      k[g] = T.k[t];
+      f[g] = T.k[t] + T.m[t];
+      height[g] = T.height[t];
+      info.factor_entries += (int64_t)T.k[t] * (T.k[t] + 1) / 2 + (int64_t)T.k[t] * T.m[t];
+    }
+  }
+  for (int g = 0; g < nf; ++g) {
+    Foff[g + 1] = Foff[g] + (int64_t)f[g] * f[g];
+    rowoff[g + 1] = rowoff[g] + f[g];
+    info.max_front = std::max(info.max_front, f[g]);
+    if ((int64_t)f[g] * f[g] >= (int64_t)1 << 31) throw HzError{HZ_EINVAL, "front too large"};
+  }
+  info.front_entries = Foff[nf];
+  std::vector<int> rows(rowoff[nf]), cmap(rowoff[nf], -1);
+  std::vector<int64_t> amap_ptr(nf + 1, 0);
+  std::vector<int> amap_pos;
+  std::vector<int64_t> amap_val;
+  std::vector<double2> Aval;
+  for (size_t i = 0; i < ns; ++i) {
+    const FrontTree& T = *trees[i];
+    const CsrC& A = *mats[i];
+    const int64_t aoff = (int64_t)Aval.size();
+    for (const cplx& v : A.val) Aval.push_back(make_double2(v.real(), v.imag()));
+    const int ntf = (int)T.k.size();
+    // front position of a local row v inside front t
+    auto front_pos = [&](int t, int32_t v) -> int {
+      int p = T.pos[v];
+      if (p >= T.piv_begin[t] && p < T.piv_begin[t] + T.k[t]) return (int)(p - T.piv_begin[t]);
+      const int32_t* ub = &T.upd[T.upd_ptr[t]];
+      int lo = 0, hi = T.m[t];
+      while (lo < hi) {  // update rows are sorted by elimination position
+        int mid = (lo + hi) / 2;
+        if (T.pos[ub[mid]] < p)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      if (lo >= T.m[t] || ub[lo] != v) return -1;
+      return T.k[t] + lo;
+    };
+    for (int t = 0; t < ntf; ++t) {
+      const int g = base[i] + t;
+      int64_t ro = rowoff[g];
+      for (int r = 0; r < T.k[t]; ++r) rows[ro + r] = (int)(sub_off[i] + T.perm[T.piv_begin[t] + r]);
+      for (int q = 0; q < T.m[t]; ++q) rows[ro + T.k[t] + q] = (int)(sub_off[i] + T.upd[T.upd_ptr[t] + q]);
+      if (T.parent[t] >= 0)
+        for (int q = 0; q < T.m[t]; ++q) {
+          int pp = front_pos(T.parent[t], T.upd[T.upd_ptr[t] + q]);
+          if (pp < 0) throw HzError{HZ_EINTERNAL, "update row missing from the parent front"};
+          cmap[ro + T.k[t] + q] = pp;
+        }
+      else if (T.m[t] != 0)
+        throw HzError{HZ_EINTERNAL, "root front with update rows"};
+      for (int32_t c : T.children[t]) child_idx.push_back(base[i] + c);
+      child_ptr[g + 1] = (int)child_idx.size();
+      // lower-triangle entries (in elimination order) of the pivot columns
+      for (int cj = 0; cj < T.k[t]; ++cj) {
+        const int32_t v = T.perm[T.piv_begin[t] + cj];
+        for (int64_t p = A.rowptr[v]; p < A.rowptr[v + 1]; ++p) {
+          const int32_t r = A.col[p];
+          if (T.pos[r] < T.pos[v]) continue;
+          int rp = front_pos(t, r);
+          if (rp < 0) throw HzError{HZ_EINTERNAL, "matrix entry outside its front"};
+          amap_pos.push_back(rp + cj * f[g]);
+          amap_val.push_back(aoff + p);
+        }
+      }
+      amap_ptr[g + 1] = (int64_t)amap_pos.size();
+    }
+  }
+  // level schedule by tree height
+  int maxh = 0;
+  for (int g = 0; g < nf; ++g) maxh = std::max(maxh, height[g]);
+  info.nlevels = maxh + 1;
+  info.nfronts = nf;
+  info.level_ptr.assign(maxh + 2, 0);
+  for (int g = 0; g < nf; ++g) info.level_ptr[height[g] + 1]++;
+  for (int l = 0; l <= maxh; ++l) info.level_ptr[l + 1] += info.level_ptr[l];
+  std::vector<int> level_list(nf);
+  {
+    std::vector<int> fill(info.level_ptr.begin(), info.level_ptr.end() - 1);
+    for (int g = 0; g < nf; ++g) level_list[fill[height[g]]++] = g;
+  }
+  mf.nfronts = nf;
+  mf.nlevels = info.nlevels;
+  mf.max_f = info.max_front;
+  mf.rows_total = rowoff[nf];
+  mf.F_total = Foff[nf];
+  mf.amap_total = (int64_t)amap_pos.size();
+  mf.level_ptr_h = info.level_ptr.data();
+  mf.level_list = pool.upload(level_list, st);
+  mf.k = pool.upload(k, st);
+  mf.f = pool.upload(f, st);
+  mf.Foff = pool.upload(Foff, st);
+  mf.rowoff = pool.upload(rowoff, st);
+  mf.rows = pool.upload(rows, st);
+  mf.cmap = pool.upload(cmap, st);
+  mf.child_ptr = pool.upload(child_ptr, st);
+  mf.child_idx = pool.upload(child_idx, st);
+  mf.amap_ptr = pool.upload(amap_ptr, st);
+  mf.amap_pos = pool.upload(amap_pos, st);
+  mf.amap_val = pool.upload(amap_val, st);
+  mf.Aval = pool.upload(Aval, st);
+  mf.F = pool.alloc<double2>(Foff[nf]);
+  mf.perturbed = pool.alloc<int>(1);
+  CK(cudaMemsetAsync(mf.perturbed, 0, sizeof(int), st));
+}
+
+void upload_split(const CsrC& A, DevSplitCsr& D, DevPool& pool, cudaStream_t st) {
+  CsrR re, im;
+  split_re_im(A, re, im);
+  D.n = A.nrows;
+  D.ncols = A.ncols;
+  D.nnz_re = (int64_t)re.col.size();
+  D.nnz_im = (int64_t)im.col.size();
+  D.rp_re = pool.upload(re.rowptr, st);
+  D.col_re = pool.upload(re.col, st);
+  D.val_re = pool.upload(re.val, st);
+  D.rp_im = pool.upload(im.rowptr, st);
+  D.col_im = pool.upload(im.col, st);
+  D.val_im = pool.upload(im.val, st);
+}
+
+struct DevReal {
+  int64_t n = 0;
+  int64_t* rp = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+};
+void upload_real(const CsrR& A, DevReal& D, DevPool& pool, cudaStream_t st) {
+  D.n = A.nrows;
+  D.rp = pool.upload(A.rowptr, st);
+  D.col = pool.upload(A.col, st);
+  D.val = pool.upload(A.val, st);
+}
+
+struct LevelDev {             // one level of ORAS on the device
+  DevMF mf;
+  MFHost info;
+  int64_t n = 0, sub_rows = 0;
+  std::vector<FrontTree> trees;
+  double amax = 0.0;
+};
+
+void build_level(const Space& sp, const std::vector<Subdomain>& subs, int leaf, LevelDev& L, DevPool& pool,
+                 cudaStream_t st) {
+  const size_t np = subs.size();
+  std::vector<int64_t> sub_off(np + 1, 0);
+  for (size_t i = 0; i < np; ++i) sub_off[i + 1] = sub_off[i] + (int64_t)subs[i].dofs.size();
+  if (sub_off[np] >= (int64_t)1 << 31) throw HzError{HZ_EINVAL, "subdomain rows exceed 2^31"};
+  L.n = sp.n;
+  L.sub_rows = sub_off[np];
+  L.trees.resize(np);
+  std::vector<const CsrC*> mats(np);
+  std::vector<const FrontTree*> tr(np);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (long i = 0; i < (long)np; ++i) {
+    std::vector<double> X(3 * subs[i].dofs.size());
+    for (size_t l = 0; l < subs[i].dofs.size(); ++l)
+      for (int d = 0; d < 3; ++d) X[3 * l + d] = sp.coords[3 * subs[i].dofs[l] + d];
+    L.trees[i] = nd_symbolic(subs[i].A, X, leaf);
+  }
+  for (size_t i = 0; i < np; ++i) {
+    mats[i] = &subs[i].A;
+    tr[i] = &L.trees[i];
+    for (const cplx& v : subs[i].A.val) L.amax = std::max(L.amax, std::abs(v));
+  }
+  build_mf(mats, tr, sub_off, L.mf, L.info, pool, st);
+  std::vector<int> gidx(sub_off[np]), own(sp.n, -1);
+  for (size_t i = 0; i < np; ++i)
+    for (size_t l = 0; l < subs[i].dofs.size(); ++l) {
+      gidx[sub_off[i] + l] = (int)subs[i].dofs[l];
+      if (subs[i].owned[l]) own[subs[i].dofs[l]] = (int)(sub_off[i] + l);
+    }
+  for (int64_t g = 0; g < sp.n; ++g)
+    if (own[g] < 0) throw HzError{HZ_EINTERNAL, "dof without owning subdomain"};
+  L.mf.nsub_rows = sub_off[np];
+  L.mf.gidx = pool.upload(gidx, st);
+  L.mf.own = pool.upload(own, st);
+}
+
+// A single "subdomain" covering the whole matrix: direct factorisation.
+void build_direct(const Space& sp, const CsrC& A, int leaf, LevelDev& L, DevPool& pool, cudaStream_t st) {
+  std::vector<Subdomain> one(1);
+  one[0].dofs.resize(sp.n);
+  std::iota(one[0].dofs.begin(), one[0].dofs.end(), 0);
+  one[0].owned.assign(sp.n, 1);
+  one[0].A = A;
+  build_level(sp, one, leaf, L, pool, st);
+}
+
+void mesh_from_abi(const hz_mesh* in, Mesh& m) {
+  if (!in || !in->xyz || !in->tets || in->nv <= 0 || in->ne <= 0) throw HzError{HZ_EINVAL, "empty or NULL mesh"};
+  if (in->nbf < 0 || (in->nbf > 0 && (!in->bfaces || !in->bface_tag)))
+    throw HzError{HZ_EINVAL, "boundary face arrays missing"};
+  if (in->nv >= (int64_t)1 << 31) throw HzError{HZ_EINVAL, "too many vertices"};
+  m.nv = in->nv;
+  m.ne = in->ne;
+  m.xyz.assign(in->xyz, in->xyz + 3 * in->nv);
+  m.tets.assign(in->tets, in->tets + 4 * in->ne);
+  m.bfaces.assign(in->bfaces, in->bfaces + 3 * in->nbf);
+  m.btag.assign(in->bface_tag, in->bface_tag + in->nbf);
+  for (int32_t v : m.bfaces)
+    if (v < 0 || v >= m.nv) throw HzError{HZ_EINVAL, "boundary face vertex out of range"};
+}
+
+}  // namespace
+
+struct hz_ctx {
+  hz_options opt;
+  cudaStream_t st = nullptr;
+  DevPool pool;
+  Mesh fine, coarse;
+  Space space;
+  CsrC A_host;
+  DevSplitCsr A;
+  LevelDev lf;                // fine ORAS level
+  bool has_coarse = false;
+  Space cspace;
+  DevSplitCsr E;
+  DevReal Z, ZT;
+  LevelDev lc;                // coarse ORAS level (or direct factors of E)
+  int perturbed = 0;
+  double setup_s = 0, factor_s = 0;
+  // workspaces (capacity s_cap columns)
+  int s_cap = 0;
+  DevPool work;
+  double2 *B = nullptr, *X = nullptr, *R = nullptr, *T = nullptr, *Q = nullptr, *Xsub = nullptr, *U = nullptr;
+  double2 *rH = nullptr, *yH = nullptr, *XsubH = nullptr;
+  DevKrylov Kout, Kin;
+  double* bnorm = nullptr;
+  double* rnorm = nullptr;
+  double* h_res = nullptr;    // pinned host
+  int* h_done = nullptr;
+  int* d_srcidx = nullptr;
+  double2* d_srcval = nullptr;
+  int src_cap = 0;
+};
+
+namespace {
+
+void alloc_krylov(DevKrylov& K, int64_t n, int s, int m, DevPool& p) {
+  K.n = n;
+  K.s = s;
+  K.m = m;
+  K.nblk = 304;
+  K.V = p.alloc<double2>((size_t)(m + 1) * n * s);
+  K.Zk = p.alloc<double2>((size_t)m * n * s);
+  K.W = p.alloc<double2>((size_t)n * s);
+  K.H = p.alloc<double2>((size_t)s * (m + 1) * m);
+  K.hpart = p.alloc<double2>((size_t)K.nblk * (m + 1) * s);
+  K.h1 = p.alloc<double2>((size_t)(m + 1) * s);
+  K.h2 = p.alloc<double2>((size_t)(m + 1) * s);
+  K.cs = p.alloc<double>((size_t)s * m);
+  K.sn = p.alloc<double2>((size_t)s * m);
+  K.g = p.alloc<double2>((size_t)s * (m + 1));
+  K.y = p.alloc<double2>((size_t)s * m);
+  K.beta = p.alloc<double>(s);
+  K.res = p.alloc<double>(s);
+  K.tol = p.alloc<double>(s);
+  K.kc = p.alloc<int>(s);
+  K.done = p.alloc<int>(s);
+}
+
+void ensure_workspace(hz_ctx* c, int s) {
+  if (s <= c->s_cap) {
+    c->Kout.s = s;
+    c->Kin.s = s;
+    return;
+  }
+  CK(cudaStreamSynchronize(c->st));
+  c->work.release();
+  if (c->h_res) cudaFreeHost(c->h_res);
+  if (c->h_done) cudaFreeHost(c->h_done);
+  c->h_res = nullptr;
+  c->h_done = nullptr;
+  c->s_cap = 0;
+  const int64_t n = c->space.n;
+  DevPool& p = c->work;
+  c->B = p.alloc<double2>(n * s);
+  c->X = p.alloc<double2>(n * s);
+  c->R = p.alloc<double2>(n * s);
+  c->T = p.alloc<double2>(n * s);
+  c->Q = p.alloc<double2>(n * s);
+  c->U = p.alloc<double2>(n * s);
+  c->Xsub = p.alloc<double2>(c->lf.sub_rows * s);
+  c->lf.mf.W = p.alloc<double2>(c->lf.mf.rows_total * s);
+  c->lf.mf.s_cap = s;
+  alloc_krylov(c->Kout, n, s, c->opt.restart, p);
+  if (c->has_coarse) {
+    const int64_t nh = c->cspace.n;
+    c->rH = p.alloc<double2>(nh * s);
+    c->yH = p.alloc<double2>(nh * s);
+    c->XsubH = p.alloc<double2>(c->lc.sub_rows * s);
+    c->lc.mf.W = p.alloc<double2>(c->lc.mf.rows_total * s);
+    c->lc.mf.s_cap = s;
+    if (c->opt.coarse_mode == HZ_COARSE_GMRES) {
+      alloc_krylov(c->Kin, nh, s, std::max(1, c->opt.coarse_inner_its), p);
+      CK(cudaMemsetAsync(c->Kin.tol, 0, s * sizeof(double), c->st));
+    }
+  }
+  c->bnorm = p.alloc<double>(s);
+  c->rnorm = p.alloc<double>(s);
+  CK(cudaMallocHost(&c->h_res, 2 * s * sizeof(double)));
+  CK(cudaMallocHost(&c->h_done, s * sizeof(int)));
+  c->s_cap = s;
+}
+
+// ORAS on one level: Z = sum_i R_i^T D_i A_i^{-1} R_i V (+ Qadd)
+void apply_oras(LevelDev& L, const double2* V, double2* Zout, const double2* Qadd, double2* Xsub, int s,
+                cudaStream_t st) {
+  gather_rows(L.mf.gidx, L.sub_rows, V, Xsub, s, st);
+  mf_solve(L.mf, Xsub, s, st);
+  scatter_owned(L.mf.own, L.n, Xsub, Qadd, Zout, s, st);
+}
+
+// y_H ~ E^{-1} r_H
+void coarse_solve(hz_ctx* c, const double2* rH, double2* yH, int s) {
+  cudaStream_t st = c->st;
+  const int64_t nh = c->cspace.n;
+  if (c->opt.coarse_mode == HZ_COARSE_DIRECT) {
+    apply_oras(c->lc, rH, yH, nullptr, c->XsubH, s, st);
+    return;
+  }
+  DevKrylov& K = c->Kin;
+  K.s = s;
+  axpy_cols_zero(yH, nh * s, st);
+  krylov_start(K, rH, st);
+  const int64_t vs = nh * s;
+  for (int j = 0; j < K.m; ++j) {
+    apply_oras(c->lc, K.V + j * vs, K.Zk + j * vs, nullptr, c->XsubH, s, st);
+    spmm_split(c->E, K.Zk + j * vs, K.W, nullptr, s, 0, st);
+    krylov_arnoldi(K, j, st);
+  }
+  krylov_update(K, yH, st);
+}
+
+// Zout = M^{-1} V (Eq. 2lvl; Eq. oras without a coarse level)
+void apply_prec(hz_ctx* c, const double2* V, double2* Zout, int s) {
+  cudaStream_t st = c->st;
+  if (!c->has_coarse) {
+    apply_oras(c->lf, V, Zout, nullptr, c->Xsub, s, st);
+    return;
+  }
+  spmm_real(c->ZT.n, c->ZT.rp, c->ZT.col, c->ZT.val, V, c->rH, s, st);   // r_H = Z^T v
+  coarse_solve(c, c->rH, c->yH, s);                                       // y_H ~ E^{-1} r_H
+  spmm_real(c->Z.n, c->Z.rp, c->Z.col, c->Z.val, c->yH, c->Q, s, st);    // q = Z y_H
+  spmm_split(c->A, c->Q, c->T, V, s, 1, st);                              // t = v - A q
+  apply_oras(c->lf, c->T, Zout, c->Q, c->Xsub, s, st);                    // z = M1^{-1} t + q
+}
+
+// Flexible GMRES on the block c->B (n x s, row-major); solution in c->X.
+int fgmres(hz_ctx* c, int s, hz_stats* stats) {
+  cudaStream_t st = c->st;
+  const int64_t n = c->space.n;
+  DevKrylov& K = c->Kout;
+  K.s = s;
+  const int m = c->opt.restart;
+  const int64_t vs = n * s;
+  axpy_cols_zero(c->X, vs, st);
+  column_norms(c->B, n, s, c->bnorm, K, st);
+  std::vector<double> bn(s), tol(s);
+  CK(cudaMemcpyAsync(c->h_res, c->bnorm, s * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int q = 0; q < s; ++q) {
+    bn[q] = c->h_res[q];
+    tol[q] = c->opt.rtol * bn[q];
+  }
+  CK(cudaMemcpyAsync(K.tol, tol.data(), s * sizeof(double), cudaMemcpyHostToDevice, st));
+  cast_copy(c->B, c->R, vs, st);
+  int its = 0, restarts = 0;
+  bool all_conv = false;
+  double maxrel = 0.0;
+  while (true) {
+    krylov_start(K, c->R, st);
+    for (int j = 0; j < m && its < c->opt.maxit; ++j) {
+      apply_prec(c, K.V + j * vs, K.Zk + j * vs, s);
+      spmm_split(c->A, K.Zk + j * vs, K.W, nullptr, s, 0, st);
+      krylov_arnoldi(K, j, st);
+      ++its;
+      CK(cudaMemcpyAsync(c->h_done, K.done, s * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      bool alldone = true;
+      for (int q = 0; q < s; ++q) alldone &= c->h_done[q] != 0;
+      if (alldone) break;
+    }
+    krylov_update(K, c->X, st);
+    spmm_split(c->A, c->X, c->R, c->B, s, 1, st);  // true residual R = B - A X
+    column_norms(c->R, n, s, c->rnorm, K, st);
+    CK(cudaMemcpyAsync(c->h_res, c->rnorm, s * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    all_conv = true;
+    maxrel = 0.0;
+    for (int q = 0; q < s; ++q) {
+      double rel = bn[q] > 0 ? c->h_res[q] / bn[q] : 0.0;
+      maxrel = std::max(maxrel, rel);
+      all_conv &= rel <= c->opt.rtol;
+    }
+    if (c->opt.verbose)
+      fprintf(stderr, "[hz] fgmres cycle %d its %d max rel residual %.3e\n", restarts, its, maxrel);
+    if (all_conv || its >= c->opt.maxit) break;
+    ++restarts;
+  }
+  if (stats) {
+    stats->iterations = its;
+    stats->restarts = restarts;
+    stats->converged = all_conv ? 1 : 0;
+    stats->ncols = s;
+    stats->max_rel_residual = maxrel;
+  }
+  return all_conv ? HZ_OK : HZ_ENOTCONV;
+}
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    return f();
+  } catch (const HzError& e) {
+    return fail(e.code, e.msg);
+  } catch (const CudaFail& e) {
+    return fail(HZ_ECUDA, std::string(e.what) + ": " + cudaGetErrorString(e.e));
+  } catch (const std::bad_alloc&) {
+    return fail(HZ_ENOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(HZ_EINTERNAL, e.what());
+  }
+}
+
+void check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw CudaFail{e, "kernel launch"};
+}
+
+}  // namespace
+
+extern "C" {
+
+int hz_default_options(hz_options* o) {
+  if (!o) return fail(HZ_EINVAL, "NULL options");
+  o->precision = HZ_PREC_FP64;
+  o->rtol = 1e-6;
+  o->maxit = 500;
+  o->restart = 30;
+  o->max_block = 64;
+  o->coarse_mode = HZ_COARSE_GMRES;
+  o->coarse_inner_its = 10;
+  o->leaf_size = 64;
+  o->pivot_tau = 1e-12;
+  o->verbose = 0;
+  return HZ_OK;
+}
+
+int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const int32_t* elem_part, int32_t nparts,
+             const hz_mesh* coarse, const hz_options* opt, void* stream, hz_ctx** out) {
+  if (!out) return fail(HZ_EINVAL, "NULL output pointer");
+  *out = nullptr;
+  std::unique_ptr<hz_ctx> c(new hz_ctx());
+  int rc = guarded([&]() -> int {
+    const double t0 = now_s();
+    if (opt)
+      c->opt = *opt;
+    else
+      hz_default_options(&c->opt);
+    const hz_options& o = c->opt;
+    if (!(freq_hz > 0)) throw HzError{HZ_EINVAL, "frequency must be positive"};
+    if (!velocity || !elem_part || nparts <= 0) throw HzError{HZ_EINVAL, "velocity / partition missing"};
+    if (o.precision != HZ_PREC_FP64 && o.precision != HZ_PREC_MIXED) throw HzError{HZ_EINVAL, "bad precision"};
+    if (o.restart < 1 || o.maxit < 1 || o.max_block < 1 || o.max_block > 64 || !(o.rtol > 0) || o.leaf_size < 1)
+      throw HzError{HZ_EINVAL, "bad Krylov options"};
+    if (o.coarse_mode < 0 || o.coarse_mode > 2) throw HzError{HZ_EINVAL, "bad coarse_mode"};
+    if (o.coarse_mode != HZ_COARSE_NONE && !coarse) throw HzError{HZ_EINVAL, "coarse mesh required"};
+    if (o.coarse_mode == HZ_COARSE_GMRES && o.coarse_inner_its < 1) throw HzError{HZ_EINVAL, "coarse_inner_its < 1"};
+    c->st = (cudaStream_t)stream;
+    mesh_from_abi(fine, c->fine);
+    mesh_build_adjacency(c->fine);
+    const int64_t ne = c->fine.ne;
+    std::vector<double> mvals(ne);
+    for (int64_t e = 0; e < ne; ++e) {
+      if (!(velocity[e] > 0) || !std::isfinite(velocity[e])) throw HzError{HZ_EINVAL, "velocity must be > 0"};
+      mvals[e] = 1.0 / (velocity[e] * velocity[e]);
+    }
+    std::vector<int32_t> part(elem_part, elem_part + ne);
+    std::vector<int64_t> pc(nparts, 0);
+    for (int32_t p : part) {
+      if (p < 0 || p >= nparts) throw HzError{HZ_EINVAL, "element partition out of range"};
+      pc[p]++;
+    }
+    for (int64_t v : pc)
+      if (v == 0) throw HzError{HZ_EINVAL, "empty subdomain in the partition"};
+    const double omega = 2.0 * M_PI * freq_hz;
+    c->space = p3_space(c->fine);
+    if (c->space.n >= (int64_t)1 << 31) throw HzError{HZ_EINVAL, "more than 2^31 dofs"};
+    c->A_host = assemble_global(c->fine, c->space, mvals, omega);
+    upload_split(c->A_host, c->A, c->pool, c->st);
+    std::vector<Subdomain> subs = build_subdomains(c->fine, c->space, part, nparts, mvals, omega);
+    build_level(c->space, subs, o.leaf_size, c->lf, c->pool, c->st);
+    subs.clear();
+    if (o.coarse_mode != HZ_COARSE_NONE) {
+      c->has_coarse = true;
+      mesh_from_abi(coarse, c->coarse);
+      CoarseSpace C = build_coarse(c->fine, c->space, mvals, part, omega, c->coarse);
+      c->cspace = C.space;
+      upload_split(C.E, c->E, c->pool, c->st);
+      upload_real(C.Z, c->Z, c->pool, c->st);
+      upload_real(C.ZT, c->ZT, c->pool, c->st);
+      if (o.coarse_mode == HZ_COARSE_GMRES) {
+        std::vector<Subdomain> csubs = build_subdomains(c->coarse, c->cspace, C.part, nparts, C.mvals, omega);
+        build_level(c->cspace, csubs, o.leaf_size, c->lc, c->pool, c->st);
+      } else {
+        build_direct(c->cspace, C.E, o.leaf_size, c->lc, c->pool, c->st);
+      }
+    }
+    CK(cudaStreamSynchronize(c->st));
+    const double t1 = now_s();
+    mf_factor(c->lf.mf, o.pivot_tau * c->lf.amax, c->st);
+    check_launch();
+    if (c->has_coarse) {
+      mf_factor(c->lc.mf, o.pivot_tau * c->lc.amax, c->st);
+      check_launch();
+    }
+    int pf = 0, pcnt = 0;
+    CK(cudaMemcpyAsync(&pf, c->lf.mf.perturbed, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    if (c->has_coarse) CK(cudaMemcpyAsync(&pcnt, c->lc.mf.perturbed, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    c->factor_s = now_s() - t1;
+    c->perturbed = pf + pcnt;
+    if (o.pivot_tau == 0.0 && c->perturbed) throw HzError{HZ_ESINGULAR, "zero pivot in a local factorisation"};
+    c->setup_s = now_s() - t0;
+    if (o.verbose)
+      fprintf(stderr, "[hz] setup n=%lld nnz=%lld fronts=%d levels=%d max_front=%d factor %.3fs total %.3fs\n",
+              (long long)c->space.n, (long long)c->A_host.col.size(), c->lf.info.nfronts, c->lf.info.nlevels,
+              c->lf.info.max_front, c->factor_s, c->setup_s);
+    return HZ_OK;
+  });
+  if (rc != HZ_OK) {
+    if (c) {
+      cudaStreamSynchronize(c->st);
+      c->pool.release();
+    }
+    return rc;
+  }
+  *out = c.release();
+  return HZ_OK;
+}
+
+int hz_ndof(const hz_ctx* c, int64_t* n) {
+  if (!c || !n) return fail(HZ_EINVAL, "NULL argument");
+  *n = c->space.n;
+  return HZ_OK;
+}
+
+int hz_dof_coords(const hz_ctx* c, double* xyz) {
+  if (!c || !xyz) return fail(HZ_EINVAL, "NULL argument");
+  std::memcpy(xyz, c->space.coords.data(), c->space.coords.size() * sizeof(double));
+  return HZ_OK;
+}
+
+int hz_get_info(const hz_ctx* c, hz_info* info) {
+  if (!c || !info) return fail(HZ_EINVAL, "NULL argument");
+  std::memset(info, 0, sizeof(*info));
+  info->n = c->space.n;
+  info->nnz = (int64_t)c->A_host.col.size();
+  info->nnz_imag = c->A.nnz_im;
+  info->nparts = (int32_t)c->lf.trees.size();
+  info->sub_rows = c->lf.sub_rows;
+  info->n_coarse = c->has_coarse ? c->cspace.n : 0;
+  info->nnz_coarse = c->has_coarse ? c->E.nnz_re : 0;
+  info->factor_entries = c->lf.info.factor_entries;
+  info->coarse_factor_entries = c->has_coarse ? c->lc.info.factor_entries : 0;
+  info->front_entries = c->lf.info.front_entries;
+  info->max_front = c->lf.info.max_front;
+  info->nfronts = c->lf.info.nfronts;
+  info->nlevels = c->lf.info.nlevels;
+  info->perturbed_pivots = c->perturbed;
+  info->device_bytes = c->pool.bytes + c->work.bytes;
+  return HZ_OK;
+}
+
+int hz_matrix_csr(const hz_ctx* c, int64_t* rowptr, int32_t* col, double* val) {
+  if (!c || !rowptr || !col || !val) return fail(HZ_EINVAL, "NULL argument");
+  const CsrC& A = c->A_host;
+  std::memcpy(rowptr, A.rowptr.data(), A.rowptr.size() * sizeof(int64_t));
+  std::memcpy(col, A.col.data(), A.col.size() * sizeof(int32_t));
+  for (size_t i = 0; i < A.val.size(); ++i) {
+    val[2 * i] = A.val[i].real();
+    val[2 * i + 1] = A.val[i].imag();
+  }
+  return HZ_OK;
+}
+
+// Copy an [s][n] complex block from the caller into c->B (rows layout).
+static void load_block(hz_ctx* c, const double* F, int s, int on_device) {
+  const int64_t n = c->space.n;
+  const double2* src = reinterpret_cast<const double2*>(F);
+  if (!on_device) {
+    CK(cudaMemcpyAsync(c->U, F, (size_t)n * s * sizeof(double2), cudaMemcpyHostToDevice, c->st));
+    src = c->U;
+  }
+  transpose_to_rows(src, c->B, n, s, c->st);
+}
+
+static void store_block(hz_ctx* c, const double2* Brow, double* out, int s, int on_device) {
+  const int64_t n = c->space.n;
+  double2* dst = on_device ? reinterpret_cast<double2*>(out) : c->U;
+  transpose_from_rows(Brow, dst, n, s, c->st);
+  if (!on_device) CK(cudaMemcpyAsync(out, c->U, (size_t)n * s * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+}
+
+int hz_apply_A(hz_ctx* c, const double* X, double* Y, int32_t s, int32_t on_device) {
+  if (!c || !X || !Y || s < 1 || s > c->opt.max_block) return fail(HZ_EINVAL, "bad argument");
+  return guarded([&]() -> int {
+    ensure_workspace(c, s);
+    load_block(c, X, s, on_device);
+    spmm_split(c->A, c->B, c->R, nullptr, s, 0, c->st);
+    check_launch();
+    store_block(c, c->R, Y, s, on_device);
+    return HZ_OK;
+  });
+}
+
+int hz_apply_prec(hz_ctx* c, const double* X, double* Y, int32_t s, int32_t on_device) {
+  if (!c || !X || !Y || s < 1 || s > c->opt.max_block) return fail(HZ_EINVAL, "bad argument");
+  return guarded([&]() -> int {
+    ensure_workspace(c, s);
+    load_block(c, X, s, on_device);
+    apply_prec(c, c->B, c->R, s);
+    check_launch();
+    store_block(c, c->R, Y, s, on_device);
+    return HZ_OK;
+  });
+}
+
+int hz_solve_rhs(hz_ctx* c, const double* F, int32_t ns, int32_t F_on_device, double* u, int32_t u_on_device,
+                 hz_stats* stats) {
+  if (!c || !F || !u || ns < 0) return fail(HZ_EINVAL, "bad argument");
+  return guarded([&]() -> int {
+    const double t0 = now_s();
+    const int64_t n = c->space.n;
+    int rc = HZ_OK;
+    hz_stats agg;
+    std::memset(&agg, 0, sizeof(agg));
+    agg.converged = 1;
+    for (int q0 = 0; q0 < ns; q0 += c->opt.max_block) {
+      const int s = std::min(c->opt.max_block, ns - q0);
+      ensure_workspace(c, s);
+      load_block(c, F + 2 * (size_t)q0 * n, s, F_on_device);
+      hz_stats st1;
+      int r = fgmres(c, s, &st1);
+      check_launch();
+      store_block(c, c->X, u + 2 * (size_t)q0 * n, s, u_on_device);
+      if (r != HZ_OK) rc = r;
+      agg.iterations = std::max(agg.iterations, st1.iterations);
+      agg.restarts += st1.restarts;
+      agg.converged &= st1.converged;
+      agg.max_rel_residual = std::max(agg.max_rel_residual, st1.max_rel_residual);
+    }
+    agg.ncols = ns;
+    agg.solve_seconds = now_s() - t0;
+    agg.setup_seconds = c->setup_s;
+    agg.factor_seconds = c->factor_s;
+    if (stats) *stats = agg;
+    if (rc != HZ_OK) g_last_error = "FGMRES reached maxit before rtol";
+    return rc;
+  });
+}
+
+int hz_solve(hz_ctx* c, const double* src_xyz, const double* src_amp, int32_t ns, double* u, int32_t u_on_device,
+             hz_stats* stats) {
+  if (!c || !src_xyz || !src_amp || !u || ns < 0) return fail(HZ_EINVAL, "bad argument");
+  return guarded([&]() -> int {
+    const double t0 = now_s();
+    const int64_t n = c->space.n;
+    std::vector<int64_t> elem(ns);
+    std::vector<double> lam(4 * (size_t)ns);
+    locate_points(c->fine, src_xyz, ns, elem.data(), lam.data());
+    for (int q = 0; q < ns; ++q)
+      if (elem[q] < 0) throw HzError{HZ_EINVAL, "source outside the mesh"};
+    int rc = HZ_OK;
+    hz_stats agg;
+    std::memset(&agg, 0, sizeof(agg));
+    agg.converged = 1;
+    for (int q0 = 0; q0 < ns; q0 += c->opt.max_block) {
+      const int s = std::min(c->opt.max_block, ns - q0);
+      ensure_workspace(c, s);
+      std::vector<int> idx;
+      std::vector<double2> val;
+      for (int q = 0; q < s; ++q) {
+        double phi[NLOC];
+        p3_basis(&lam[4 * (q0 + q)], phi);
+        const double ar = src_amp[2 * (q0 + q)], ai = src_amp[2 * (q0 + q) + 1];
+        for (int i = 0; i < NLOC; ++i) {
+          int64_t g = c->space.l2g[NLOC * elem[q0 + q] + i];
+          if (c->space.dirichlet[g]) continue;
+          idx.push_back((int)(g * s + q));
+          val.push_back(make_double2(ar * phi[i], ai * phi[i]));
+        }
+      }
+      if ((int)idx.size() > c->src_cap) {
+        CK(cudaStreamSynchronize(c->st));
+        if (c->d_srcidx) cudaFree(c->d_srcidx);
+        if (c->d_srcval) cudaFree(c->d_srcval);
+        c->d_srcidx = nullptr;
+        c->d_srcval = nullptr;
+        CK(cudaMalloc(&c->d_srcidx, idx.size() * sizeof(int)));
+        CK(cudaMalloc(&c->d_srcval, val.size() * sizeof(double2)));
+        c->src_cap = (int)idx.size();
+      }
+      CK(cudaMemcpyAsync(c->d_srcidx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+      CK(cudaMemcpyAsync(c->d_srcval, val.data(), val.size() * sizeof(double2), cudaMemcpyHostToDevice, c->st));
+      axpy_cols_zero(c->B, n * s, c->st);
+      scatter_point_sources(c->B, n, s, c->d_srcidx, c->d_srcval, (int)idx.size(), c->st);
+      hz_stats st1;
+      int r = fgmres(c, s, &st1);
+      check_launch();
+      store_block(c, c->X, u + 2 * (size_t)q0 * n, s, u_on_device);
+      if (r != HZ_OK) rc = r;
+      agg.iterations = std::max(agg.iterations, st1.iterations);
+      agg.restarts += st1.restarts;
+      agg.converged &= st1.converged;
+      agg.max_rel_residual = std::max(agg.max_rel_residual, st1.max_rel_residual);
+    }
+    agg.ncols = ns;
+    agg.solve_seconds = now_s() - t0;
+    agg.setup_seconds = c->setup_s;
+    agg.factor_seconds = c->factor_s;
+    if (stats) *stats = agg;
+    if (rc != HZ_OK) g_last_error = "FGMRES reached maxit before rtol";
+    return rc;
+  });
+}
+
+void hz_free(hz_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  c->work.release();
+  c->pool.release();
+  if (c->h_res) cudaFreeHost(c->h_res);
+  if (c->h_done) cudaFreeHost(c->h_done);
+  if (c->d_srcidx) cudaFree(c->d_srcidx);
+  if (c->d_srcval) cudaFree(c->d_srcval);
+  delete c;
+}
+
+const char* hz_strerror(int code) {
+  switch (code) {
+    case HZ_OK: return "ok";
+    case HZ_EINVAL: return "invalid argument";
+    case HZ_ENOMEM: return "out of memory";
+    case HZ_ECUDA: return "CUDA error";
+    case HZ_EINTERNAL: return "internal error";
+    case HZ_ESINGULAR: return "singular local matrix";
+    case HZ_ENOTCONV: return "not converged";
+    case HZ_EBREAKDOWN: return "Krylov breakdown";
+    default: return "unknown error";
+  }
+}
+
+const char* hz_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

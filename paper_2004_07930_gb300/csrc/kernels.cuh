@@ -1,0 +1,101 @@
+// Device kernels of the two-level ORAS / FGMRES hot path (declarations).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace hz {
+
+// Split complex CSR: A = A_re + i A_im, A_im holding only the entries with a
+// nonzero imaginary part (Robin faces); both share the row count.
+struct DevSplitCsr {
+  int64_t n = 0, ncols = 0, nnz_re = 0, nnz_im = 0;
+  int64_t* rp_re = nullptr;
+  int32_t* col_re = nullptr;
+  double* val_re = nullptr;
+  int64_t* rp_im = nullptr;
+  int32_t* col_im = nullptr;
+  double* val_im = nullptr;
+};
+
+// Multifrontal factors of a batch of local matrices, grouped by tree height.
+struct DevMF {
+  int64_t nfronts = 0, nsub_rows = 0, rows_total = 0, F_total = 0, amap_total = 0;
+  int nlevels = 0;
+  int max_f = 0;
+  int* level_ptr_h = nullptr;   // host [nlevels+1]
+  int* level_list = nullptr;    // device [nfronts] front ids ordered by height
+  int* k = nullptr;             // pivots per front
+  int* f = nullptr;             // front order k + m
+  int64_t* Foff = nullptr;      // offset of the f x f front (column-major)
+  int64_t* rowoff = nullptr;    // offset of the front's row list (prefix sum of f)
+  int* rows = nullptr;          // [rows_total] flat sub-vector row of each front row
+  int* cmap = nullptr;          // [rows_total] parent front position of each update row
+  int* child_ptr = nullptr;     // [nfronts+1]
+  int* child_idx = nullptr;
+  int64_t* amap_ptr = nullptr;  // [nfronts+1]
+  int* amap_pos = nullptr;      // front position r + c f of each assembled entry
+  int64_t* amap_val = nullptr;  // index into Aval
+  double2* Aval = nullptr;      // concatenated local matrix values
+  double2* F = nullptr;         // fronts: L (unit lower, D on the diagonal) in the first k columns
+  double2* W = nullptr;         // front vectors [rows_total][s_cap]
+  int s_cap = 0;
+  int* gidx = nullptr;          // [nsub_rows] global row of each sub-vector row (R_i)
+  int* own = nullptr;           // [n] sub-vector row of the owning copy (D_i Boolean)
+  int* perturbed = nullptr;     // device counter
+};
+
+// --- sparse products ---
+// Y = A X (mode 0) or Y = B - A X (mode 1); X, Y, B row-major [n][s] complex
+void spmm_split(const DevSplitCsr& A, const double2* X, double2* Y, const double2* B, int s, int mode,
+                cudaStream_t st);
+// Y = R X for a real CSR R (rows x cols) on complex blocks
+void spmm_real(int64_t nrows, const int64_t* rp, const int32_t* col, const double* val, const double2* X,
+               double2* Y, int s, cudaStream_t st);
+
+// --- restriction / prolongation ---
+void gather_rows(const int* idx, int64_t nrows, const double2* X, double2* Y, int s, cudaStream_t st);
+void scatter_owned(const int* own, int64_t n, const double2* Xsub, const double2* Q, double2* Z, int s,
+                   cudaStream_t st);
+
+// --- multifrontal ---
+void mf_factor(DevMF& mf, double pivot_tau, cudaStream_t st);
+void mf_solve(DevMF& mf, double2* Xsub, int s, cudaStream_t st);
+
+// --- Krylov (one Krylov space per column) ---
+struct DevKrylov {
+  int m = 0, s = 0;
+  int64_t n = 0;
+  double2* V = nullptr;     // [(m+1)][n][s]
+  double2* Zk = nullptr;    // [m][n][s]
+  double2* W = nullptr;     // [n][s]
+  double2* H = nullptr;     // [s][(m+1) m] Hessenberg, rotated in place
+  double2* hpart = nullptr; // partial dot products [nblk][m+1][s]
+  double2* h1 = nullptr;    // [m+1][s]
+  double2* h2 = nullptr;    // [m+1][s]
+  double* cs = nullptr;     // [s][m] Givens cosines (real)
+  double2* sn = nullptr;    // [s][m] Givens sines
+  double2* g = nullptr;     // [s][m+1]
+  double2* y = nullptr;     // [s][m]
+  double* beta = nullptr;   // [s] norms
+  double* res = nullptr;    // [s] residual estimates |g_{j+1}|
+  double* tol = nullptr;    // [s] absolute stop tolerance per column
+  int* kc = nullptr;        // [s] accepted Arnoldi steps
+  int* done = nullptr;      // [s]
+  int nblk = 0;
+};
+
+void column_norms(const double2* X, int64_t n, int s, double* out, DevKrylov& K, cudaStream_t st);
+void krylov_start(DevKrylov& K, const double2* R, cudaStream_t st);  // V0 = R/beta, g = beta e1, flags
+void krylov_arnoldi(DevKrylov& K, int j, cudaStream_t st);           // CGS2 of W against V_0..j, H, Givens
+void krylov_update(DevKrylov& K, double2* X, cudaStream_t st);        // X += Zk y
+void axpy_cols_zero(double2* X, int64_t count, cudaStream_t st);
+
+// --- right-hand sides / layout ---
+void scatter_point_sources(double2* B, int64_t n, int s, const int* idx, const double2* val, int nent,
+                           cudaStream_t st);
+void transpose_to_rows(const double2* F, double2* B, int64_t n, int s, cudaStream_t st);    // [s][n] -> [n][s]
+void transpose_from_rows(const double2* B, double2* F, int64_t n, int s, cudaStream_t st);  // [n][s] -> [s][n]
+void cast_copy(const double2* X, double2* Y, int64_t count, cudaStream_t st);
+
+}  // namespace hz

