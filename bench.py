@@ -1,0 +1,318 @@
+#!/usr/bin/env python
+"""Throughput benchmark: right-hand sides solved per second at GMRES rtol 1e-6.
+
+Workload (default): the Overthrust-like synthetic model at 5 Hz — 20 x 20 x
+4.65 km, graded Kuhn tensor grid at 1.3 P3 cells per local minimum
+wavelength, Dirichlet free surface on top and absorbing faces elsewhere,
+64 box subdomains with one element layer of overlap, a nested 2x coarser
+mesh for the coarse level, 16 surface sources at z = 100 m. One step = one
+hz_solve of the 16 sources (FGMRES + two-level ORAS to rtol 1e-6), factors
+resident on the device (setup reported separately, not timed).
+
+Both forms are measured on the same GPU: FP64 and mixed (local fronts in
+complex FP32, everything else FP64); `value` is the mixed form, `forms`
+holds both. `e2e` repeats the mixed-form step through the C ABI with host
+output buffers (device-to-host copy of the wavefields inside the timed
+region). `roofline` covers the dominant kernel family (the fine-level local
+solves), timed with CUDA events inside the library over the timed region.
+`cpu_baseline` times the CPU oracle (assembly + SuperLU) on a bounded crop
+of the same workload.
+
+Multi-GPU (torchrun): sources are independent, so every rank holds its own
+replica of the factors and solves its own 16 sources (weak scaling, no
+collective on the data path); the barrier and the max over ranks only
+frame the timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP64_NOMINAL_GFLOPS = 1250.0  # nominal GB300 FP64 rate (no FP64 figure in the measured peaks)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", choices=["overthrust5", "cube"], default="overthrust5")
+    ap.add_argument("--forms", default="mixed,fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=None, help="timed steps of the FP64 form (default: --steps)")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured", d.get("sm_max_mhz")
+    except Exception:
+        return 6800.0, "fallback", None
+
+
+def problem(cfg):
+    from paper_2004_07930_gb300 import workloads as wl
+
+    if cfg == "cube":
+        return wl.cube_problem(), "cube 1 km, 6^3 cells, P3 (6859 dofs), 2 Hz, 4 subdomains, 1 source"
+    p = wl.overthrust_problem(5.0, nparts=64, seed=0)
+    nx, ny, nz = p["fine"]["ncells"]
+    return p, ("Overthrust-like 20x20x4.65 km, 5 Hz, %dx%dx%d cells x 6 Kuhn tets, P3, 64 subdomains "
+               "(8x8x1), overlap 1, nested coarse mesh, 16 surface sources" % (nx, ny, nz))
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(budget_s=25.0):
+    """Oracle (assembly + SuperLU + triangular solves) on a bounded crop of
+    the workload: a corner of 8 x 8 cells (about 2.8 x 2.8 km, full depth)."""
+    import numpy as np
+
+    from oracle import assemble as oa
+    from paper_2004_07930_gb300 import workloads as wl
+
+    t0 = time.time()
+    p = wl.overthrust_problem(5.0, nparts=4, crop=(0.125, 0.125, 1.0),
+                              sources=[[1250.0, 1250.0, 100.0], [2000.0, 1000.0, 100.0]])
+    space, A, F = oa.system(p["fine"], p["velocity"], p["freq"], p["src_xyz"])
+    import scipy.sparse.linalg as spla
+
+    lu = spla.splu(A.tocsc())
+    u = lu.solve(F.T.copy())
+    elapsed = time.time() - t0
+    ns = F.shape[0]
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": ns / elapsed, "unit": "RHS/s", "cores": 1, "kind": "oracle",
+            "host_cores_available": cores,
+            "sample": "oracle (P3 assembly + SciPy SuperLU) on an 8x8-cell (2.8x2.8x4.65 km) corner crop of "
+                      "the same 5 Hz workload: n=%d dofs, %d sources, %.1f s total; the full 0.95M-dof "
+                      "problem is ~%.0fx larger" % (space.n, ns, elapsed, 949375.0 / space.n),
+            "n_sample": int(space.n), "seconds": elapsed}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cb = cpu_baseline()
+    out = {"impl": "reference", "metric": "RHS solved/s at rtol 1e-6", "value": cb["value"], "unit": "RHS/s",
+           "n_gpus": args.gpus, "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+           "config": {"workload": "overthrust5-crop (oracle: direct solve, no GMRES)"},
+           "cpu_baseline": cb,
+           "e2e": {"value": cb["value"], "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e):
+    prec = hz.HZ_PREC_MIXED if form == "mixed" else hz.HZ_PREC_FP64
+    t0 = time.time()
+    S = hz.Solver.from_problem(prob, precision=prec, rtol=1e-6, stream=stream)
+    setup_wall = time.time() - t0
+    info = S.info()
+    src = prob["src_xyz"]
+    ns = len(src)
+    out = torch.empty((ns, S.n), dtype=torch.complex128, device="cuda")
+    iters = []
+    for _ in range(warmup):
+        _, st = S.solve(src, out=out)
+        iters.append(st["iterations"])
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    S.profile_begin()
+    e0.record(stream)
+    stats = []
+    for _ in range(steps):
+        _, st = S.solve(src, out=out)
+        stats.append(st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = S.profile_end()
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(ms, ws)
+    res = {"rhs_per_s": ns * steps * ws / (ms / 1e3), "ms_per_step": ms / steps,
+           "iterations": [s["iterations"] for s in stats], "max_rel_residual": max(s["max_rel_residual"] for s in stats),
+           "converged": all(s["converged"] for s in stats), "setup_s": setup_wall,
+           "factor_s": stats[0]["factor_seconds"], "info": info, "phases": prof}
+    if with_e2e:
+        import numpy as np
+
+        hostbuf = np.empty((ns, S.n), dtype=np.complex128)
+        barrier(ws)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(steps):
+            S.solve(src, out=hostbuf)
+        torch.cuda.synchronize()
+        el = max_over_ranks(time.perf_counter() - t, ws)
+        res["e2e"] = {"value": ns * steps * ws / el, "unit": "RHS/s",
+                      "h2d_bytes_per_step": int(src.size * 8 + ns * 16),
+                      "d2h_bytes_per_step": int(hostbuf.nbytes)}
+    S.close()
+    return res
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    ws, rank, local = dist_env()
+    import torch
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2004_07930_gb300 import hz
+
+    hz.load()
+    prob, desc = problem(args.config)
+    stream = torch.cuda.current_stream()
+    forms = [f for f in args.forms.split(",") if f]
+    clocks = ClockSampler(local)
+    results = {}
+    for i, form in enumerate(forms):
+        steps = args.steps if (form != "fp64" or args.fp64_steps is None) else args.fp64_steps
+        if i == 0:
+            clocks.start()
+        results[form] = measure_form(prob, form, steps, args.warmup, stream, ws, torch, hz, with_e2e=(i == 0))
+        if i == 0:
+            clk = clocks.stop()
+    head = forms[0]
+    r = results[head]
+    hbm, peak_kind, _ = peaks()
+    ph = r["phases"]["fronts"]
+    es = "c64" if head == "mixed" else "c128"
+    if head == "mixed":
+        achieved = ph["bytes"] / (ph["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": "fine local solves (k_mf_fwd_gemm / k_mf_bwd_gemm, complex FP32)",
+                "peak_kind": peak_kind, "launches": ph["calls"]}
+    else:
+        achieved = ph["flops"] / (ph["ms"] / 1e3) / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
+                "frac": achieved / FP64_NOMINAL_GFLOPS, "traffic": None,
+                "kernel": "fine local solves (k_mf_fwd_gemm / k_mf_bwd_gemm, complex FP64)",
+                "peak_kind": "nominal FP64", "launches": ph["calls"]}
+    line = {
+        "metric": "RHS solved/s at rtol 1e-6", "value": r["rhs_per_s"], "unit": "RHS/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 fronts + c128 Krylov/SpMM/coarse" if head == "mixed" else "c128",
+        "data": "synthetic (seeded Overthrust-like model; no real data)",
+        "config": {"workload": desc, "n": r["info"]["n"], "nnz": r["info"]["nnz"], "sources_per_step": 16,
+                   "rtol": 1e-6, "l2_flush": "inputs larger than L2 (factors %.1f GB)" %
+                   (r["info"]["device_bytes"] / 1e9), "parallelism": "replicas x%d (sources)" % ws},
+        "roofline": roof,
+        "clocks": clk,
+        "gpu_launches": None,
+        "e2e": r.get("e2e"),
+        "forms": {f: {k: v for k, v in results[f].items() if k not in ("info",)} for f in results},
+    }
+    if "mixed" in results and "fp64" in results:
+        line["mixed_over_fp64"] = results["mixed"]["rhs_per_s"] / results["fp64"]["rhs_per_s"]
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

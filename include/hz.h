@@ -163,6 +163,27 @@ int hz_apply_A(hz_ctx* ctx, const double* X, double* Y, int32_t s, int32_t on_de
  * with HZ_COARSE_NONE), X and Y [s][n][2]. */
 int hz_apply_prec(hz_ctx* ctx, const double* X, double* Y, int32_t s, int32_t on_device);
 
+/* Per-phase device timing of the hot path (CUDA events recorded around each
+ * phase on the context's stream while profiling is on). Phases: "spmm_A"
+ * (products with A), "fronts" (fine-level local solves), "restrict_prolong"
+ * (fine R_i gathers and partition-of-unity scatters), "coarse" (Z^T, the
+ * coarse solve and Z), "arnoldi" (outer orthogonalisation, least squares and
+ * solution update). flops and bytes are the algorithmic counts of the
+ * recorded calls (complex multiply-add = 8 flops; bytes = compulsory
+ * traffic: matrix/factor entries, indices and the input/output blocks). */
+typedef struct hz_phase_time {
+  const char* name;
+  int64_t calls;
+  double ms;
+  double flops;
+  double bytes;
+} hz_phase_time;
+
+/* Reset the counters and start recording. */
+int hz_profile_begin(hz_ctx* ctx);
+/* Synchronise the stream, stop recording and write up to `cap` phases. */
+int hz_profile_end(hz_ctx* ctx, hz_phase_time* out, int32_t cap, int32_t* count);
+
 /* Host copy of A in CSR form: rowptr [n+1], col [nnz], val [nnz][2]. */
 int hz_matrix_csr(const hz_ctx* ctx, int64_t* rowptr, int32_t* col, double* val);
 

@@ -67,6 +67,13 @@ struct DevPool {
     if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
     return p;
   }
+  void free_one(void* p, size_t nbytes) {
+    auto it = std::find(ptrs.begin(), ptrs.end(), p);
+    if (it == ptrs.end()) return;
+    cudaFree(p);
+    ptrs.erase(it);
+    bytes -= nbytes;
+  }
   void release() {
     for (void* p : ptrs) cudaFree(p);
     ptrs.clear();
@@ -75,21 +82,26 @@ struct DevPool {
 };
 
 struct MFHost {
-  int64_t factor_entries = 0, front_entries = 0;
+  int64_t factor_entries = 0, front_entries = 0, stored_entries = 0;
   int max_front = 0, nfronts = 0, nlevels = 0;
-  std::vector<int> level_ptr;
+  std::vector<int> level_ptr, ftile_ptr, btile_ptr;
+  // per-level algorithmic work of one solve sweep (complex multiply-adds per column)
+  std::vector<double> fwd_cmacs, bwd_cmacs;
 };
 
 // Pack the fronts of several local matrices into one device structure;
 // sub_off[i] is the first row of subdomain i in the flat sub-vector.
+constexpr int MF_TILE = 64;  // rows per solve tile (matches the kernels)
+
 void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const FrontTree*>& trees,
-              const std::vector<int64_t>& sub_off, DevMF& mf, MFHost& info, DevPool& pool, cudaStream_t st) {
+              const std::vector<int64_t>& sub_off, bool fp32, DevMF& mf, MFHost& info, DevPool& pool,
+              cudaStream_t st) {
   const size_t ns = mats.size();
   std::vector<int> base(ns + 1, 0);
   for (size_t i = 0; i < ns; ++i) base[i + 1] = base[i] + (int)trees[i]->k.size();
   const int nf = base[ns];
   std::vector<int> k(nf), f(nf), height(nf), child_ptr(nf + 1, 0), child_idx;
-  std::vector<int64_t> Foff(nf + 1, 0), rowoff(nf + 1, 0);
+  std::vector<int64_t> Foff(nf + 1, 0), rowoff(nf + 1, 0), Moff(nf + 1, 0), Doff(nf + 1, 0);
   for (size_t i = 0; i < ns; ++i) {
     const FrontTree& T = *trees[i];
     for (size_t t = 0; t < T.k.size(); ++t) {
@@ -103,10 +115,13 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
   for (int g = 0; g < nf; ++g) {
     Foff[g + 1] = Foff[g] + (int64_t)f[g] * f[g];
     rowoff[g + 1] = rowoff[g] + f[g];
+    Moff[g + 1] = Moff[g] + (int64_t)f[g] * k[g];
+    Doff[g + 1] = Doff[g] + k[g];
     info.max_front = std::max(info.max_front, f[g]);
     if ((int64_t)f[g] * f[g] >= (int64_t)1 << 31) throw HzError{HZ_EINVAL, "front too large"};
   }
   info.front_entries = Foff[nf];
+  info.stored_entries = Moff[nf];
   std::vector<int> rows(rowoff[nf]), cmap(rowoff[nf], -1);
   std::vector<int64_t> amap_ptr(nf + 1, 0);
   std::vector<int> amap_pos;
@@ -177,6 +192,24 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
     std::vector<int> fill(info.level_ptr.begin(), info.level_ptr.end() - 1);
     for (int g = 0; g < nf; ++g) level_list[fill[height[g]]++] = g;
   }
+  // solve tiles: forward over the f rows, backward over the k pivots
+  std::vector<int2> ftiles, btiles;
+  info.ftile_ptr.assign(1, 0);
+  info.btile_ptr.assign(1, 0);
+  info.fwd_cmacs.assign(maxh + 1, 0.0);
+  info.bwd_cmacs.assign(maxh + 1, 0.0);
+  for (int l = 0; l <= maxh; ++l) {
+    for (int q = info.level_ptr[l]; q < info.level_ptr[l + 1]; ++q) {
+      const int g = level_list[q];
+      for (int r0 = 0; r0 < f[g]; r0 += MF_TILE) ftiles.push_back(make_int2(g, r0));
+      for (int j0 = 0; j0 < k[g]; j0 += MF_TILE) btiles.push_back(make_int2(g, j0));
+      const double kk = k[g], mm = f[g] - k[g];
+      info.fwd_cmacs[l] += kk * (kk + 1) / 2 + kk * mm;
+      info.bwd_cmacs[l] += kk * (kk + 1) / 2 + kk * mm;
+    }
+    info.ftile_ptr.push_back((int)ftiles.size());
+    info.btile_ptr.push_back((int)btiles.size());
+  }
   mf.nfronts = nf;
   mf.nlevels = info.nlevels;
   mf.max_f = info.max_front;
@@ -184,6 +217,18 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
   mf.F_total = Foff[nf];
   mf.amap_total = (int64_t)amap_pos.size();
   mf.level_ptr_h = info.level_ptr.data();
+  mf.ftile_ptr_h = info.ftile_ptr.data();
+  mf.btile_ptr_h = info.btile_ptr.data();
+  mf.fp32 = fp32 ? 1 : 0;
+  mf.M_total = Moff[nf];
+  mf.D_total = Doff[nf];
+  mf.ftiles = pool.upload(ftiles, st);
+  mf.btiles = pool.upload(btiles, st);
+  mf.Moff = pool.upload(Moff, st);
+  mf.Doff = pool.upload(Doff, st);
+  const size_t esz = fp32 ? sizeof(float2) : sizeof(double2);
+  mf.M = pool.alloc<char>(Moff[nf] * esz);
+  mf.Dinv = pool.alloc<char>(Doff[nf] * esz);
   mf.level_list = pool.upload(level_list, st);
   mf.k = pool.upload(k, st);
   mf.f = pool.upload(f, st);
@@ -238,8 +283,8 @@ struct LevelDev {             // one level of ORAS on the device
   double amax = 0.0;
 };
 
-void build_level(const Space& sp, const std::vector<Subdomain>& subs, int leaf, LevelDev& L, DevPool& pool,
-                 cudaStream_t st) {
+void build_level(const Space& sp, const std::vector<Subdomain>& subs, int leaf, bool fp32, LevelDev& L,
+                 DevPool& pool, cudaStream_t st) {
   const size_t np = subs.size();
   std::vector<int64_t> sub_off(np + 1, 0);
   for (size_t i = 0; i < np; ++i) sub_off[i + 1] = sub_off[i] + (int64_t)subs[i].dofs.size();
@@ -261,7 +306,7 @@ void build_level(const Space& sp, const std::vector<Subdomain>& subs, int leaf, 
     tr[i] = &L.trees[i];
     for (const cplx& v : subs[i].A.val) L.amax = std::max(L.amax, std::abs(v));
   }
-  build_mf(mats, tr, sub_off, L.mf, L.info, pool, st);
+  build_mf(mats, tr, sub_off, fp32, L.mf, L.info, pool, st);
   std::vector<int> gidx(sub_off[np]), own(sp.n, -1);
   for (size_t i = 0; i < np; ++i)
     for (size_t l = 0; l < subs[i].dofs.size(); ++l) {
@@ -276,13 +321,14 @@ void build_level(const Space& sp, const std::vector<Subdomain>& subs, int leaf, 
 }
 
 // A single "subdomain" covering the whole matrix: direct factorisation.
-void build_direct(const Space& sp, const CsrC& A, int leaf, LevelDev& L, DevPool& pool, cudaStream_t st) {
+void build_direct(const Space& sp, const CsrC& A, int leaf, bool fp32, LevelDev& L, DevPool& pool,
+                  cudaStream_t st) {
   std::vector<Subdomain> one(1);
   one[0].dofs.resize(sp.n);
   std::iota(one[0].dofs.begin(), one[0].dofs.end(), 0);
   one[0].owned.assign(sp.n, 1);
   one[0].A = A;
-  build_level(sp, one, leaf, L, pool, st);
+  build_level(sp, one, leaf, fp32, L, pool, st);
 }
 
 void mesh_from_abi(const hz_mesh* in, Mesh& m) {
@@ -302,8 +348,50 @@ void mesh_from_abi(const hz_mesh* in, Mesh& m) {
 
 }  // namespace
 
+enum Phase { PH_SPMM = 0, PH_FRONTS, PH_RESTRICT, PH_COARSE, PH_ARNOLDI, PH_COUNT };
+static const char* PHASE_NAMES[PH_COUNT] = {"spmm_A", "fronts", "restrict_prolong", "coarse", "arnoldi"};
+
+// CUDA-event timing of hot-path phases (off unless hz_profile_begin)
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  struct Rec {
+    int ph;
+    cudaEvent_t a, b;
+    double flops, bytes;
+  };
+  std::vector<Rec> recs;
+  cudaEvent_t ev() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) throw HzError{HZ_ECUDA, "cudaEventCreate failed"};
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  int begin(int ph, cudaStream_t st) {
+    if (!on) return -1;
+    Rec r{ph, ev(), ev(), 0.0, 0.0};
+    CK(cudaEventRecord(r.a, st));
+    recs.push_back(r);
+    return (int)recs.size() - 1;
+  }
+  void end(int id, cudaStream_t st, double flops, double bytes) {
+    if (id < 0) return;
+    CK(cudaEventRecord(recs[id].b, st));
+    recs[id].flops = flops;
+    recs[id].bytes = bytes;
+  }
+  void destroy() {
+    for (auto e : pool) cudaEventDestroy(e);
+    pool.clear();
+  }
+};
+
 struct hz_ctx {
   hz_options opt;
+  Profiler prof;
   cudaStream_t st = nullptr;
   DevPool pool;
   Mesh fine, coarse;
@@ -379,16 +467,20 @@ void ensure_workspace(hz_ctx* c, int s) {
   c->T = p.alloc<double2>(n * s);
   c->Q = p.alloc<double2>(n * s);
   c->U = p.alloc<double2>(n * s);
-  c->Xsub = p.alloc<double2>(c->lf.sub_rows * s);
-  c->lf.mf.W = p.alloc<double2>(c->lf.mf.rows_total * s);
+  const size_t ef = c->lf.mf.fp32 ? sizeof(float2) : sizeof(double2);
+  c->Xsub = (double2*)p.alloc<char>(c->lf.sub_rows * s * ef);
+  c->lf.mf.Win = p.alloc<char>(c->lf.mf.rows_total * s * ef);
+  c->lf.mf.Wout = p.alloc<char>(c->lf.mf.rows_total * s * ef);
   c->lf.mf.s_cap = s;
   alloc_krylov(c->Kout, n, s, c->opt.restart, p);
   if (c->has_coarse) {
     const int64_t nh = c->cspace.n;
     c->rH = p.alloc<double2>(nh * s);
     c->yH = p.alloc<double2>(nh * s);
-    c->XsubH = p.alloc<double2>(c->lc.sub_rows * s);
-    c->lc.mf.W = p.alloc<double2>(c->lc.mf.rows_total * s);
+    const size_t ec = c->lc.mf.fp32 ? sizeof(float2) : sizeof(double2);
+    c->XsubH = (double2*)p.alloc<char>(c->lc.sub_rows * s * ec);
+    c->lc.mf.Win = p.alloc<char>(c->lc.mf.rows_total * s * ec);
+    c->lc.mf.Wout = p.alloc<char>(c->lc.mf.rows_total * s * ec);
     c->lc.mf.s_cap = s;
     if (c->opt.coarse_mode == HZ_COARSE_GMRES) {
       alloc_krylov(c->Kin, nh, s, std::max(1, c->opt.coarse_inner_its), p);
@@ -404,10 +496,28 @@ void ensure_workspace(hz_ctx* c, int s) {
 
 // ORAS on one level: Z = sum_i R_i^T D_i A_i^{-1} R_i V (+ Qadd)
 void apply_oras(LevelDev& L, const double2* V, double2* Zout, const double2* Qadd, double2* Xsub, int s,
-                cudaStream_t st) {
-  gather_rows(L.mf.gidx, L.sub_rows, V, Xsub, s, st);
+                cudaStream_t st, Profiler* prof = nullptr) {
+  const double es = L.mf.fp32 ? 8.0 : 16.0;
+  // gather: indices + read V rows + write sub-vector; scatter: owner index + read + (q) + write
+  const double rbytes = 4.0 * L.sub_rows + (16.0 + es) * L.sub_rows * s + 4.0 * L.n +
+                        (es + 16.0 + (Qadd ? 16.0 : 0.0)) * L.n * s;
+  const double fbytes = es * 2.0 * L.info.factor_entries + 2.0 * es * s * L.sub_rows;
+  const double fflops = 8.0 * s * 2.0 * L.info.factor_entries;
+  int p0 = prof ? prof->begin(PH_RESTRICT, st) : -1;
+  if (L.mf.fp32)
+    gather_rows_f32(L.mf.gidx, L.sub_rows, V, (float2*)Xsub, s, st);
+  else
+    gather_rows(L.mf.gidx, L.sub_rows, V, Xsub, s, st);
+  if (prof) prof->end(p0, st, 0.0, 0.0);
+  int p1 = prof ? prof->begin(PH_FRONTS, st) : -1;
   mf_solve(L.mf, Xsub, s, st);
-  scatter_owned(L.mf.own, L.n, Xsub, Qadd, Zout, s, st);
+  if (prof) prof->end(p1, st, fflops, fbytes);
+  int p2 = prof ? prof->begin(PH_RESTRICT, st) : -1;
+  if (L.mf.fp32)
+    scatter_owned_f32(L.mf.own, L.n, (const float2*)Xsub, Qadd, Zout, s, st);
+  else
+    scatter_owned(L.mf.own, L.n, Xsub, Qadd, Zout, s, st);
+  if (prof) prof->end(p2, st, 0.0, rbytes);
 }
 
 // y_H ~ E^{-1} r_H
@@ -431,18 +541,35 @@ void coarse_solve(hz_ctx* c, const double2* rH, double2* yH, int s) {
   krylov_update(K, yH, st);
 }
 
+// algorithmic cost of Y = A X (split real/imaginary CSR, complex block of s)
+static void spmm_cost(const DevSplitCsr& A, int s, bool with_b, double& flops, double& bytes) {
+  const double nz = (double)(A.nnz_re + A.nnz_im);
+  flops = 4.0 * nz * s;
+  bytes = 12.0 * nz + 16.0 * (A.n + 1) + 16.0 * A.ncols * s + 16.0 * A.n * s * (with_b ? 2.0 : 1.0);
+}
+
+void spmm_A(hz_ctx* c, const double2* X, double2* Y, const double2* B, int s, int mode) {
+  double fl, by;
+  spmm_cost(c->A, s, mode == 1, fl, by);
+  int id = c->prof.begin(PH_SPMM, c->st);
+  spmm_split(c->A, X, Y, B, s, mode, c->st);
+  c->prof.end(id, c->st, fl, by);
+}
+
 // Zout = M^{-1} V (Eq. 2lvl; Eq. oras without a coarse level)
 void apply_prec(hz_ctx* c, const double2* V, double2* Zout, int s) {
   cudaStream_t st = c->st;
   if (!c->has_coarse) {
-    apply_oras(c->lf, V, Zout, nullptr, c->Xsub, s, st);
+    apply_oras(c->lf, V, Zout, nullptr, c->Xsub, s, st, &c->prof);
     return;
   }
+  int id = c->prof.begin(PH_COARSE, st);
   spmm_real(c->ZT.n, c->ZT.rp, c->ZT.col, c->ZT.val, V, c->rH, s, st);   // r_H = Z^T v
   coarse_solve(c, c->rH, c->yH, s);                                       // y_H ~ E^{-1} r_H
   spmm_real(c->Z.n, c->Z.rp, c->Z.col, c->Z.val, c->yH, c->Q, s, st);    // q = Z y_H
-  spmm_split(c->A, c->Q, c->T, V, s, 1, st);                              // t = v - A q
-  apply_oras(c->lf, c->T, Zout, c->Q, c->Xsub, s, st);                    // z = M1^{-1} t + q
+  c->prof.end(id, st, 0.0, 0.0);
+  spmm_A(c, c->Q, c->T, V, s, 1);                                         // t = v - A q
+  apply_oras(c->lf, c->T, Zout, c->Q, c->Xsub, s, st, &c->prof);          // z = M1^{-1} t + q
 }
 
 // Flexible GMRES on the block c->B (n x s, row-major); solution in c->X.
@@ -471,8 +598,12 @@ int fgmres(hz_ctx* c, int s, hz_stats* stats) {
     krylov_start(K, c->R, st);
     for (int j = 0; j < m && its < c->opt.maxit; ++j) {
       apply_prec(c, K.V + j * vs, K.Zk + j * vs, s);
-      spmm_split(c->A, K.Zk + j * vs, K.W, nullptr, s, 0, st);
+      spmm_A(c, K.Zk + j * vs, K.W, nullptr, s, 0);
+      int id = c->prof.begin(PH_ARNOLDI, st);
       krylov_arnoldi(K, j, st);
+      // two CGS passes (dots + update) over V_0..j and W, a norm and a scale
+      c->prof.end(id, st, 2.0 * 2.0 * 8.0 * n * (j + 1) * s,
+                  16.0 * n * s * (4.0 * (j + 1) + 6.0));
       ++its;
       CK(cudaMemcpyAsync(c->h_done, K.done, s * sizeof(int), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
@@ -481,7 +612,7 @@ int fgmres(hz_ctx* c, int s, hz_stats* stats) {
       if (alldone) break;
     }
     krylov_update(K, c->X, st);
-    spmm_split(c->A, c->X, c->R, c->B, s, 1, st);  // true residual R = B - A X
+    spmm_A(c, c->X, c->R, c->B, s, 1);  // true residual R = B - A X
     column_norms(c->R, n, s, c->rnorm, K, st);
     CK(cudaMemcpyAsync(c->h_res, c->rnorm, s * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -593,8 +724,9 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
     if (c->space.n >= (int64_t)1 << 31) throw HzError{HZ_EINVAL, "more than 2^31 dofs"};
     c->A_host = assemble_global(c->fine, c->space, mvals, omega);
     upload_split(c->A_host, c->A, c->pool, c->st);
+    const bool mixed = o.precision == HZ_PREC_MIXED;
     std::vector<Subdomain> subs = build_subdomains(c->fine, c->space, part, nparts, mvals, omega);
-    build_level(c->space, subs, o.leaf_size, c->lf, c->pool, c->st);
+    build_level(c->space, subs, o.leaf_size, mixed, c->lf, c->pool, c->st);
     subs.clear();
     if (o.coarse_mode != HZ_COARSE_NONE) {
       c->has_coarse = true;
@@ -606,9 +738,9 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
       upload_real(C.ZT, c->ZT, c->pool, c->st);
       if (o.coarse_mode == HZ_COARSE_GMRES) {
         std::vector<Subdomain> csubs = build_subdomains(c->coarse, c->cspace, C.part, nparts, C.mvals, omega);
-        build_level(c->cspace, csubs, o.leaf_size, c->lc, c->pool, c->st);
+        build_level(c->cspace, csubs, o.leaf_size, mixed, c->lc, c->pool, c->st);
       } else {
-        build_direct(c->cspace, C.E, o.leaf_size, c->lc, c->pool, c->st);
+        build_direct(c->cspace, C.E, o.leaf_size, mixed, c->lc, c->pool, c->st);
       }
     }
     CK(cudaStreamSynchronize(c->st));
@@ -624,6 +756,13 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
     if (c->has_coarse) CK(cudaMemcpyAsync(&pcnt, c->lc.mf.perturbed, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     c->factor_s = now_s() - t1;
+    // the f x f workspaces are only needed by the factorisation
+    c->pool.free_one(c->lf.mf.F, c->lf.mf.F_total * sizeof(double2));
+    c->lf.mf.F = nullptr;
+    if (c->has_coarse) {
+      c->pool.free_one(c->lc.mf.F, c->lc.mf.F_total * sizeof(double2));
+      c->lc.mf.F = nullptr;
+    }
     c->perturbed = pf + pcnt;
     if (o.pivot_tau == 0.0 && c->perturbed) throw HzError{HZ_ESINGULAR, "zero pivot in a local factorisation"};
     c->setup_s = now_s() - t0;
@@ -675,6 +814,41 @@ int hz_get_info(const hz_ctx* c, hz_info* info) {
   info->perturbed_pivots = c->perturbed;
   info->device_bytes = c->pool.bytes + c->work.bytes;
   return HZ_OK;
+}
+
+int hz_profile_begin(hz_ctx* c) {
+  if (!c) return fail(HZ_EINVAL, "NULL context");
+  return guarded([&]() -> int {
+    CK(cudaStreamSynchronize(c->st));
+    c->prof.recs.clear();
+    c->prof.used = 0;
+    c->prof.on = true;
+    return HZ_OK;
+  });
+}
+
+int hz_profile_end(hz_ctx* c, hz_phase_time* out, int32_t cap, int32_t* count) {
+  if (!c || !out || !count || cap < 0) return fail(HZ_EINVAL, "bad argument");
+  return guarded([&]() -> int {
+    CK(cudaStreamSynchronize(c->st));
+    c->prof.on = false;
+    hz_phase_time acc[PH_COUNT];
+    for (int p = 0; p < PH_COUNT; ++p) acc[p] = hz_phase_time{PHASE_NAMES[p], 0, 0.0, 0.0, 0.0};
+    for (auto& r : c->prof.recs) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, r.a, r.b));
+      acc[r.ph].calls++;
+      acc[r.ph].ms += ms;
+      acc[r.ph].flops += r.flops;
+      acc[r.ph].bytes += r.bytes;
+    }
+    c->prof.recs.clear();
+    c->prof.used = 0;
+    int nout = std::min<int>(cap, PH_COUNT);
+    for (int p = 0; p < nout; ++p) out[p] = acc[p];
+    *count = nout;
+    return HZ_OK;
+  });
 }
 
 int hz_matrix_csr(const hz_ctx* c, int64_t* rowptr, int32_t* col, double* val) {
@@ -840,6 +1014,7 @@ void hz_free(hz_ctx* c) {
   if (c->h_done) cudaFreeHost(c->h_done);
   if (c->d_srcidx) cudaFree(c->d_srcidx);
   if (c->d_srcval) cudaFree(c->d_srcval);
+  c->prof.destroy();
   delete c;
 }
 

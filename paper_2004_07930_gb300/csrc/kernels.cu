@@ -141,184 +141,6 @@ void scatter_owned(const int* own, int64_t n, const double2* Xsub, const double2
 }
 
 // ---------------------------------------------------------------------------
-// Multifrontal LDL^T (complex symmetric, no pivoting, static perturbation).
-// One CTA per front; all fronts of one tree height across all subdomains in
-// one launch.
-// ---------------------------------------------------------------------------
-__global__ void k_mf_assemble(const int* __restrict__ list, const int* __restrict__ kk, const int* __restrict__ ff,
-                              const int64_t* __restrict__ Foff, const int64_t* __restrict__ rowoff,
-                              const int* __restrict__ cmap, const int* __restrict__ child_ptr,
-                              const int* __restrict__ child_idx, const int64_t* __restrict__ amap_ptr,
-                              const int* __restrict__ amap_pos, const int64_t* __restrict__ amap_val,
-                              const double2* __restrict__ Aval, double2* __restrict__ F) {
-  const int t = list[blockIdx.x];
-  const int f = ff[t];
-  double2* Ft = F + Foff[t];
-  const int64_t ff2 = (int64_t)f * f;
-  for (int64_t i = threadIdx.x; i < ff2; i += blockDim.x) Ft[i] = make_double2(0.0, 0.0);
-  __syncthreads();
-  for (int64_t p = amap_ptr[t] + threadIdx.x; p < amap_ptr[t + 1]; p += blockDim.x)
-    Ft[amap_pos[p]] = cadd(Ft[amap_pos[p]], Aval[amap_val[p]]);
-  __syncthreads();
-  for (int q = child_ptr[t]; q < child_ptr[t + 1]; ++q) {
-    const int ch = child_idx[q];
-    const int kc = kk[ch], fc = ff[ch], mc = fc - kc;
-    const double2* Fc = F + Foff[ch];
-    const int* cm = cmap + rowoff[ch] + kc;
-    const int64_t mm = (int64_t)mc * mc;
-    for (int64_t i = threadIdx.x; i < mm; i += blockDim.x) {
-      int a = (int)(i % mc), b = (int)(i / mc);
-      if (a < b) continue;
-      int64_t dst = cm[a] + (int64_t)cm[b] * f;
-      Ft[dst] = cadd(Ft[dst], Fc[(kc + a) + (int64_t)(kc + b) * fc]);
-    }
-    __syncthreads();
-  }
-}
-
-__global__ void k_mf_factor(const int* __restrict__ list, const int* __restrict__ kk, const int* __restrict__ ff,
-                            const int64_t* __restrict__ Foff, double2* __restrict__ F, double tau_abs,
-                            int* perturbed) {
-  extern __shared__ double2 col[];
-  __shared__ double2 dinv_s;
-  const int t = list[blockIdx.x];
-  const int f = ff[t], k = kk[t];
-  double2* Ft = F + Foff[t];
-  for (int j = 0; j < k; ++j) {
-    if (threadIdx.x == 0) {
-      double2 d = Ft[j + (int64_t)j * f];
-      double ad = sqrt(cabs2(d));
-      if (ad < tau_abs) {
-        d = ad > 0.0 ? make_double2(d.x / ad * tau_abs, d.y / ad * tau_abs) : make_double2(tau_abs, 0.0);
-        Ft[j + (int64_t)j * f] = d;
-        atomicAdd(perturbed, 1);
-      }
-      dinv_s = cdiv(make_double2(1.0, 0.0), d);
-    }
-    for (int r = j + 1 + threadIdx.x; r < f; r += blockDim.x) col[r] = Ft[r + (int64_t)j * f];
-    __syncthreads();
-    const double2 dinv = dinv_s;
-    for (int r = j + 1 + threadIdx.x; r < f; r += blockDim.x) Ft[r + (int64_t)j * f] = cmul(col[r], dinv);
-    const int nn = f - j - 1;
-    const int64_t nn2 = (int64_t)nn * nn;
-    for (int64_t i = threadIdx.x; i < nn2; i += blockDim.x) {
-      int r = j + 1 + (int)(i % nn), c = j + 1 + (int)(i / nn);
-      if (r < c) continue;
-      int64_t o = r + (int64_t)c * f;
-      Ft[o] = cfms(col[r], cmul(col[c], dinv), Ft[o]);
-    }
-    __syncthreads();
-  }
-}
-
-void mf_factor(DevMF& mf, double tau_abs, cudaStream_t st) {
-  size_t shm = (size_t)std::max(mf.max_f, 1) * sizeof(double2);
-  cudaFuncSetAttribute(k_mf_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-  for (int l = 0; l < mf.nlevels; ++l) {
-    int b = mf.level_ptr_h[l], e = mf.level_ptr_h[l + 1];
-    if (e == b) continue;
-    k_mf_assemble<<<e - b, 256, 0, st>>>(mf.level_list + b, mf.k, mf.f, mf.Foff, mf.rowoff, mf.cmap, mf.child_ptr,
-                                         mf.child_idx, mf.amap_ptr, mf.amap_pos, mf.amap_val, mf.Aval, mf.F);
-    k_mf_factor<<<e - b, 256, shm, st>>>(mf.level_list + b, mf.k, mf.f, mf.Foff, mf.F, tau_abs, mf.perturbed);
-  }
-}
-
-// Forward substitution L z = b and z / D, front-wise; the update rows of the
-// front vector carry L21 z to the parent (extend-add of update vectors).
-__global__ void k_mf_fwd(const int* __restrict__ list, const int* __restrict__ kk, const int* __restrict__ ff,
-                         const int64_t* __restrict__ Foff, const int64_t* __restrict__ rowoff,
-                         const int* __restrict__ rows, const int* __restrict__ cmap, const int* __restrict__ child_ptr,
-                         const int* __restrict__ child_idx, const double2* __restrict__ F, double2* __restrict__ W,
-                         double2* __restrict__ Xsub, int s) {
-  const int t = list[blockIdx.x];
-  const int f = ff[t], k = kk[t];
-  const double2* Ft = F + Foff[t];
-  const int* rt = rows + rowoff[t];
-  double2* fv = W + rowoff[t] * s;
-  const int fs = f * s;
-  for (int i = threadIdx.x; i < fs; i += blockDim.x) {
-    int r = i / s, c = i - r * s;
-    fv[i] = r < k ? Xsub[(int64_t)rt[r] * s + c] : make_double2(0.0, 0.0);
-  }
-  __syncthreads();
-  for (int q = child_ptr[t]; q < child_ptr[t + 1]; ++q) {
-    const int ch = child_idx[q];
-    const int kc = kk[ch], mc = ff[ch] - kc;
-    const double2* fvc = W + rowoff[ch] * s + (int64_t)kc * s;
-    const int* cm = cmap + rowoff[ch] + kc;
-    for (int i = threadIdx.x; i < mc * s; i += blockDim.x) {
-      int a = i / s, c = i - a * s;
-      fv[cm[a] * s + c] = cadd(fv[cm[a] * s + c], fvc[i]);
-    }
-    __syncthreads();
-  }
-  for (int j = 0; j < k; ++j) {
-    const double2* Lj = Ft + (int64_t)j * f;
-    const int nn = (f - j - 1) * s;
-    for (int i = threadIdx.x; i < nn; i += blockDim.x) {
-      int r = j + 1 + i / s, c = i % s;
-      fv[r * s + c] = cfms(Lj[r], fv[j * s + c], fv[r * s + c]);
-    }
-    __syncthreads();
-  }
-  for (int i = threadIdx.x; i < k * s; i += blockDim.x) {
-    int r = i / s, c = i - r * s;
-    Xsub[(int64_t)rt[r] * s + c] = cdiv(fv[i], Ft[r + (int64_t)r * f]);
-  }
-}
-
-// Backward substitution L^T x = y, front-wise from the root down; the update
-// rows read the already final values of the ancestors' pivots.
-__global__ void k_mf_bwd(const int* __restrict__ list, const int* __restrict__ kk, const int* __restrict__ ff,
-                         const int64_t* __restrict__ Foff, const int64_t* __restrict__ rowoff,
-                         const int* __restrict__ rows, const double2* __restrict__ F, double2* __restrict__ W,
-                         double2* __restrict__ Xsub, int s) {
-  const int t = list[blockIdx.x];
-  const int f = ff[t], k = kk[t];
-  const double2* Ft = F + Foff[t];
-  const int* rt = rows + rowoff[t];
-  double2* fv = W + rowoff[t] * s;
-  for (int i = threadIdx.x; i < f * s; i += blockDim.x) {
-    int r = i / s, c = i - r * s;
-    fv[i] = Xsub[(int64_t)rt[r] * s + c];
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = k - 1; j >= 0; --j) {
-    const double2* Lj = Ft + (int64_t)j * f;
-    for (int c = warp; c < s; c += nw) {
-      double2 acc = make_double2(0.0, 0.0);
-      for (int r = j + 1 + lane; r < f; r += 32) acc = cfma(Lj[r], fv[r * s + c], acc);
-      for (int o = 16; o > 0; o >>= 1) {
-        acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
-        acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
-      }
-      if (lane == 0) fv[j * s + c] = csub(fv[j * s + c], acc);
-    }
-    __syncthreads();
-  }
-  for (int i = threadIdx.x; i < k * s; i += blockDim.x) {
-    int r = i / s, c = i - r * s;
-    Xsub[(int64_t)rt[r] * s + c] = fv[i];
-  }
-}
-
-void mf_solve(DevMF& mf, double2* Xsub, int s, cudaStream_t st) {
-  for (int l = 0; l < mf.nlevels; ++l) {
-    int b = mf.level_ptr_h[l], e = mf.level_ptr_h[l + 1];
-    if (e == b) continue;
-    k_mf_fwd<<<e - b, 256, 0, st>>>(mf.level_list + b, mf.k, mf.f, mf.Foff, mf.rowoff, mf.rows, mf.cmap,
-                                    mf.child_ptr, mf.child_idx, mf.F, mf.W, Xsub, s);
-  }
-  for (int l = mf.nlevels - 1; l >= 0; --l) {
-    int b = mf.level_ptr_h[l], e = mf.level_ptr_h[l + 1];
-    if (e == b) continue;
-    k_mf_bwd<<<e - b, 256, 0, st>>>(mf.level_list + b, mf.k, mf.f, mf.Foff, mf.rowoff, mf.rows, mf.F, mf.W, Xsub,
-                                    s);
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Krylov: one Arnoldi process per column, CGS2 orthogonalisation (K8),
 // Givens QR of the Hessenberg matrix (K10), solution update (K12).
 // ---------------------------------------------------------------------------

@@ -19,15 +19,24 @@ struct DevSplitCsr {
 };
 
 // Multifrontal factors of a batch of local matrices, grouped by tree height.
+// Factor storage per front t: X_t (f x k, column-major) = first k columns of
+// [[L11,0],[L21,I]]^{-1}, and 1/D (k); FP64 or FP32 (mixed form).
 struct DevMF {
-  int64_t nfronts = 0, nsub_rows = 0, rows_total = 0, F_total = 0, amap_total = 0;
+  int64_t nfronts = 0, nsub_rows = 0, rows_total = 0, F_total = 0, amap_total = 0, M_total = 0, D_total = 0;
   int nlevels = 0;
   int max_f = 0;
+  int fp32 = 0;
   int* level_ptr_h = nullptr;   // host [nlevels+1]
+  int* ftile_ptr_h = nullptr;   // host [nlevels+1] forward tiles per level
+  int* btile_ptr_h = nullptr;   // host [nlevels+1] backward tiles per level
   int* level_list = nullptr;    // device [nfronts] front ids ordered by height
+  int2* ftiles = nullptr;       // (front, first row) of every forward tile
+  int2* btiles = nullptr;       // (front, first pivot) of every backward tile
   int* k = nullptr;             // pivots per front
   int* f = nullptr;             // front order k + m
-  int64_t* Foff = nullptr;      // offset of the f x f front (column-major)
+  int64_t* Foff = nullptr;      // offset of the f x f front workspace (column-major)
+  int64_t* Moff = nullptr;      // offset of X_t in M
+  int64_t* Doff = nullptr;      // offset of 1/D in Dinv
   int64_t* rowoff = nullptr;    // offset of the front's row list (prefix sum of f)
   int* rows = nullptr;          // [rows_total] flat sub-vector row of each front row
   int* cmap = nullptr;          // [rows_total] parent front position of each update row
@@ -37,8 +46,11 @@ struct DevMF {
   int* amap_pos = nullptr;      // front position r + c f of each assembled entry
   int64_t* amap_val = nullptr;  // index into Aval
   double2* Aval = nullptr;      // concatenated local matrix values
-  double2* F = nullptr;         // fronts: L (unit lower, D on the diagonal) in the first k columns
-  double2* W = nullptr;         // front vectors [rows_total][s_cap]
+  double2* F = nullptr;         // factorisation workspace (freed after setup)
+  void* M = nullptr;            // X_t factors (double2 or float2)
+  void* Dinv = nullptr;         // 1/D (double2 or float2)
+  void* Win = nullptr;          // front vectors [rows_total][s_cap]
+  void* Wout = nullptr;
   int s_cap = 0;
   int* gidx = nullptr;          // [nsub_rows] global row of each sub-vector row (R_i)
   int* own = nullptr;           // [n] sub-vector row of the owning copy (D_i Boolean)
@@ -59,8 +71,11 @@ void scatter_owned(const int* own, int64_t n, const double2* Xsub, const double2
                    cudaStream_t st);
 
 // --- multifrontal ---
-void mf_factor(DevMF& mf, double pivot_tau, cudaStream_t st);
-void mf_solve(DevMF& mf, double2* Xsub, int s, cudaStream_t st);
+void mf_factor(DevMF& mf, double tau_abs, cudaStream_t st);
+void mf_solve(DevMF& mf, void* Xsub, int s, cudaStream_t st);   // Xsub double2 or float2 (mf.fp32)
+void gather_rows_f32(const int* idx, int64_t nrows, const double2* X, float2* Y, int s, cudaStream_t st);
+void scatter_owned_f32(const int* own, int64_t n, const float2* Xsub, const double2* Q, double2* Z, int s,
+                       cudaStream_t st);
 
 // --- Krylov (one Krylov space per column) ---
 struct DevKrylov {

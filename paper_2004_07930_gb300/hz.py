@@ -19,7 +19,7 @@ HZ_PREC_FP64, HZ_PREC_MIXED = 0, 1
 
 EXPORTS = ["hz_default_options", "hz_setup", "hz_ndof", "hz_dof_coords", "hz_get_info", "hz_solve",
            "hz_solve_rhs", "hz_apply_A", "hz_apply_prec", "hz_matrix_csr", "hz_free", "hz_strerror",
-           "hz_last_error"]
+           "hz_last_error", "hz_profile_begin", "hz_profile_end"]
 
 
 class HzMesh(C.Structure):
@@ -53,6 +53,11 @@ class HzInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class HzPhaseTime(C.Structure):
+    _fields_ = [("name", C.c_char_p), ("calls", C.c_int64), ("ms", C.c_double), ("flops", C.c_double),
+                ("bytes", C.c_double)]
+
+
 _LIB = None
 
 
@@ -81,6 +86,8 @@ def load():
     lib.hz_apply_A.argtypes = [P, P, P, C.c_int32, C.c_int32]
     lib.hz_apply_prec.argtypes = [P, P, P, C.c_int32, C.c_int32]
     lib.hz_matrix_csr.argtypes = [P, P, P, P]
+    lib.hz_profile_begin.argtypes = [P]
+    lib.hz_profile_end.argtypes = [P, C.POINTER(HzPhaseTime), C.c_int32, C.POINTER(C.c_int32)]
     lib.hz_free.argtypes = [P]
     lib.hz_free.restype = None
     lib.hz_strerror.argtypes = [C.c_int]
@@ -200,6 +207,17 @@ class Solver:
         val = np.empty(nnz, dtype=np.complex128)
         _check(self._lib.hz_matrix_csr(self._ctx, rp.ctypes.data, col.ctypes.data, val.ctypes.data))
         return sp.csr_matrix((val, col, rp), shape=(self.n, self.n))
+
+    def profile_begin(self):
+        _check(self._lib.hz_profile_begin(self._ctx))
+
+    def profile_end(self):
+        """{phase: {calls, ms, flops, bytes}} since profile_begin()."""
+        arr = (HzPhaseTime * 16)()
+        cnt = C.c_int32()
+        _check(self._lib.hz_profile_end(self._ctx, arr, 16, C.byref(cnt)))
+        return {arr[i].name.decode(): dict(calls=arr[i].calls, ms=arr[i].ms, flops=arr[i].flops,
+                                           bytes=arr[i].bytes) for i in range(cnt.value)}
 
     # ---- block calls: arrays [s, n] complex128 (NumPy on host, torch on device)
     def _io(self, X):
