@@ -49,7 +49,9 @@ def parse():
     ap.add_argument("--config", choices=["overthrust5", "cube"], default="overthrust5")
     ap.add_argument("--forms", default="mixed,fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--fp64-steps", type=int, default=None, help="timed steps of the FP64 form (default: --steps)")
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the FP64 form")
+    ap.add_argument("--fp64-warmup", type=int, default=1, help="warm-up steps of the FP64 form")
+    ap.add_argument("--variants", default="one_level", help="extra preconditioner variants of the headline form")
     return ap.parse_args()
 
 
@@ -192,10 +194,10 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e):
+def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, **opts):
     prec = hz.HZ_PREC_MIXED if form == "mixed" else hz.HZ_PREC_FP64
     t0 = time.time()
-    S = hz.Solver.from_problem(prob, precision=prec, rtol=1e-6, stream=stream)
+    S = hz.Solver.from_problem(prob, precision=prec, rtol=1e-6, stream=stream, **opts)
     setup_wall = time.time() - t0
     info = S.info()
     src = prob["src_xyz"]
@@ -221,7 +223,7 @@ def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e):
     barrier(ws)
     ms = e0.elapsed_time(e1)
     ms = max_over_ranks(ms, ws)
-    res = {"rhs_per_s": ns * steps * ws / (ms / 1e3), "ms_per_step": ms / steps,
+    res = {"rhs_per_s": ns * steps * ws / (ms / 1e3), "ms_per_step": ms / steps, "steps": steps, "warmup": warmup,
            "iterations": [s["iterations"] for s in stats], "max_rel_residual": max(s["max_rel_residual"] for s in stats),
            "converged": all(s["converged"] for s in stats), "setup_s": setup_wall,
            "factor_s": stats[0]["factor_seconds"], "info": info, "phases": prof}
@@ -265,12 +267,18 @@ def main():
     clocks = ClockSampler(local)
     results = {}
     for i, form in enumerate(forms):
-        steps = args.steps if (form != "fp64" or args.fp64_steps is None) else args.fp64_steps
+        steps = args.steps if form != "fp64" else args.fp64_steps
+        warm = args.warmup if form != "fp64" else args.fp64_warmup
         if i == 0:
             clocks.start()
-        results[form] = measure_form(prob, form, steps, args.warmup, stream, ws, torch, hz, with_e2e=(i == 0))
+        results[form] = measure_form(prob, form, steps, warm, stream, ws, torch, hz, with_e2e=(i == 0))
         if i == 0:
             clk = clocks.stop()
+    variants = {}
+    for v in [x for x in args.variants.split(",") if x]:
+        if v == "one_level":
+            variants["one_level_" + forms[0]] = measure_form(prob, forms[0], args.steps, args.warmup, stream, ws,
+                                                             torch, hz, False, coarse_mode=hz.HZ_COARSE_NONE)
     head = forms[0]
     r = results[head]
     hbm, peak_kind, _ = peaks()
@@ -302,6 +310,8 @@ def main():
         "e2e": r.get("e2e"),
         "forms": {f: {k: v for k, v in results[f].items() if k not in ("info",)} for f in results},
     }
+    if variants:
+        line["variants"] = {k: {kk: vv for kk, vv in v.items() if kk not in ("info",)} for k, v in variants.items()}
     if "mixed" in results and "fp64" in results:
         line["mixed_over_fp64"] = results["mixed"]["rhs_per_s"] / results["fp64"]["rhs_per_s"]
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

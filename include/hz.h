@@ -31,8 +31,10 @@
  *   - Input arrays are read during the call and stay owned by the caller;
  *     output arrays are caller-allocated. A context owns all the device
  *     memory it allocates until hz_free.
- *   - Work is issued on the CUDA stream given to hz_setup. A context is not
- *     thread-safe; one call at a time per context.
+ *   - The library runs its kernels on a stream of its own; every call first
+ *     waits for the work already queued on the CUDA stream given to
+ *     hz_setup and returns after its own work has completed. A context is
+ *     not thread-safe; one call at a time per context.
  *   - Every int-returning call returns HZ_OK (0) or an HZ_E* code and never
  *     aborts; hz_last_error() gives a one-line description of the last error
  *     on the calling thread.
@@ -86,6 +88,8 @@ typedef struct hz_options {
   int32_t leaf_size;        /* nested-dissection leaf size (64) */
   double pivot_tau;         /* static pivot perturbation, relative to max|A_i| (1e-12) */
   int32_t verbose;          /* 0 silent */
+  int32_t use_graphs;       /* 1 (default): replay the local-solve and coarse-solve launch sequences
+                               as captured CUDA graphs; 0: launch them one by one */
 } hz_options;
 
 typedef struct hz_stats {

@@ -91,7 +91,8 @@ struct MFHost {
 
 // Pack the fronts of several local matrices into one device structure;
 // sub_off[i] is the first row of subdomain i in the flat sub-vector.
-constexpr int MF_TILE = 64;  // rows per solve tile (matches the kernels)
+constexpr int MF_FWD_ROWS = 128;  // rows per forward tile (k_mf_fwd)
+constexpr int MF_BWD_COLS = 8;    // pivots per backward tile (k_mf_bwd)
 
 void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const FrontTree*>& trees,
               const std::vector<int64_t>& sub_off, bool fp32, DevMF& mf, MFHost& info, DevPool& pool,
@@ -201,8 +202,8 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
   for (int l = 0; l <= maxh; ++l) {
     for (int q = info.level_ptr[l]; q < info.level_ptr[l + 1]; ++q) {
       const int g = level_list[q];
-      for (int r0 = 0; r0 < f[g]; r0 += MF_TILE) ftiles.push_back(make_int2(g, r0));
-      for (int j0 = 0; j0 < k[g]; j0 += MF_TILE) btiles.push_back(make_int2(g, j0));
+      for (int r0 = 0; r0 < f[g]; r0 += MF_FWD_ROWS) ftiles.push_back(make_int2(g, r0));
+      for (int j0 = 0; j0 < k[g]; j0 += MF_BWD_COLS) btiles.push_back(make_int2(g, j0));
       const double kk = k[g], mm = f[g] - k[g];
       info.fwd_cmacs[l] += kk * (kk + 1) / 2 + kk * mm;
       info.bwd_cmacs[l] += kk * (kk + 1) / 2 + kk * mm;
@@ -247,9 +248,14 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
   CK(cudaMemsetAsync(mf.perturbed, 0, sizeof(int), st));
 }
 
-void upload_split(const CsrC& A, DevSplitCsr& D, DevPool& pool, cudaStream_t st) {
+void upload_split(const CsrC& A, DevSplitCsr& D, DevPool& pool, cudaStream_t st, bool with_f32 = false) {
   CsrR re, im;
   split_re_im(A, re, im);
+  if (with_f32) {
+    std::vector<float> rf(re.val.begin(), re.val.end()), imf(im.val.begin(), im.val.end());
+    D.val_re_f = pool.upload(rf, st);
+    D.val_im_f = pool.upload(imf, st);
+  }
   D.n = A.nrows;
   D.ncols = A.ncols;
   D.nnz_re = (int64_t)re.col.size();
@@ -389,10 +395,25 @@ struct Profiler {
   }
 };
 
+// A captured CUDA graph of a fixed launch sequence, re-captured when the
+// block width or the workspace changes.
+struct GraphCache {
+  int s = -1;
+  cudaGraphExec_t exec = nullptr;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    s = -1;
+  }
+};
+
 struct hz_ctx {
   hz_options opt;
   Profiler prof;
-  cudaStream_t st = nullptr;
+  cudaStream_t st = nullptr;       // the library's own stream (graph capture needs a non-default stream)
+  cudaStream_t user_st = nullptr;  // the caller's stream: every call first waits for its pending work
+  cudaEvent_t ev_join = nullptr;
+  GraphCache g_fronts, g_coarse;
   DevPool pool;
   Mesh fine, coarse;
   Space space;
@@ -411,6 +432,7 @@ struct hz_ctx {
   DevPool work;
   double2 *B = nullptr, *X = nullptr, *R = nullptr, *T = nullptr, *Q = nullptr, *Xsub = nullptr, *U = nullptr;
   double2 *rH = nullptr, *yH = nullptr, *XsubH = nullptr;
+  float2 *rH32 = nullptr, *yH32 = nullptr;
   DevKrylov Kout, Kin;
   double* bnorm = nullptr;
   double* rnorm = nullptr;
@@ -423,14 +445,16 @@ struct hz_ctx {
 
 namespace {
 
-void alloc_krylov(DevKrylov& K, int64_t n, int s, int m, DevPool& p) {
+void alloc_krylov(DevKrylov& K, int64_t n, int s, int m, DevPool& p, bool fp32) {
   K.n = n;
   K.s = s;
   K.m = m;
+  K.fp32 = fp32 ? 1 : 0;
   K.nblk = 304;
-  K.V = p.alloc<double2>((size_t)(m + 1) * n * s);
-  K.Zk = p.alloc<double2>((size_t)m * n * s);
-  K.W = p.alloc<double2>((size_t)n * s);
+  const size_t es = fp32 ? sizeof(float2) : sizeof(double2);
+  K.V = p.alloc<char>((size_t)(m + 1) * n * s * es);
+  K.Zk = p.alloc<char>((size_t)m * n * s * es);
+  K.W = p.alloc<char>((size_t)n * s * es);
   K.H = p.alloc<double2>((size_t)s * (m + 1) * m);
   K.hpart = p.alloc<double2>((size_t)K.nblk * (m + 1) * s);
   K.h1 = p.alloc<double2>((size_t)(m + 1) * s);
@@ -453,6 +477,8 @@ void ensure_workspace(hz_ctx* c, int s) {
     return;
   }
   CK(cudaStreamSynchronize(c->st));
+  c->g_fronts.reset();
+  c->g_coarse.reset();
   c->work.release();
   if (c->h_res) cudaFreeHost(c->h_res);
   if (c->h_done) cudaFreeHost(c->h_done);
@@ -472,7 +498,7 @@ void ensure_workspace(hz_ctx* c, int s) {
   c->lf.mf.Win = p.alloc<char>(c->lf.mf.rows_total * s * ef);
   c->lf.mf.Wout = p.alloc<char>(c->lf.mf.rows_total * s * ef);
   c->lf.mf.s_cap = s;
-  alloc_krylov(c->Kout, n, s, c->opt.restart, p);
+  alloc_krylov(c->Kout, n, s, c->opt.restart, p, false);
   if (c->has_coarse) {
     const int64_t nh = c->cspace.n;
     c->rH = p.alloc<double2>(nh * s);
@@ -483,8 +509,12 @@ void ensure_workspace(hz_ctx* c, int s) {
     c->lc.mf.Wout = p.alloc<char>(c->lc.mf.rows_total * s * ec);
     c->lc.mf.s_cap = s;
     if (c->opt.coarse_mode == HZ_COARSE_GMRES) {
-      alloc_krylov(c->Kin, nh, s, std::max(1, c->opt.coarse_inner_its), p);
+      alloc_krylov(c->Kin, nh, s, std::max(1, c->opt.coarse_inner_its), p, c->lc.mf.fp32 != 0);
       CK(cudaMemsetAsync(c->Kin.tol, 0, s * sizeof(double), c->st));
+    }
+    if (c->lc.mf.fp32) {
+      c->rH32 = p.alloc<float2>(nh * s);
+      c->yH32 = p.alloc<float2>(nh * s);
     }
   }
   c->bnorm = p.alloc<double>(s);
@@ -494,9 +524,30 @@ void ensure_workspace(hz_ctx* c, int s) {
   c->s_cap = s;
 }
 
+// Replay `body` (a fixed launch sequence on st) through a captured graph.
+template <typename F>
+void run_graph(GraphCache* g, int s, cudaStream_t st, F&& body) {
+  if (!g) {
+    body();
+    return;
+  }
+  if (g->s != s || !g->exec) {
+    g->reset();
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    body();
+    CK(cudaStreamEndCapture(st, &graph));
+    cudaError_t e = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) throw CudaFail{e, "cudaGraphInstantiate"};
+    g->s = s;
+  }
+  CK(cudaGraphLaunch(g->exec, st));
+}
+
 // ORAS on one level: Z = sum_i R_i^T D_i A_i^{-1} R_i V (+ Qadd)
 void apply_oras(LevelDev& L, const double2* V, double2* Zout, const double2* Qadd, double2* Xsub, int s,
-                cudaStream_t st, Profiler* prof = nullptr) {
+                cudaStream_t st, Profiler* prof = nullptr, GraphCache* graph = nullptr) {
   const double es = L.mf.fp32 ? 8.0 : 16.0;
   // gather: indices + read V rows + write sub-vector; scatter: owner index + read + (q) + write
   const double rbytes = 4.0 * L.sub_rows + (16.0 + es) * L.sub_rows * s + 4.0 * L.n +
@@ -510,7 +561,7 @@ void apply_oras(LevelDev& L, const double2* V, double2* Zout, const double2* Qad
     gather_rows(L.mf.gidx, L.sub_rows, V, Xsub, s, st);
   if (prof) prof->end(p0, st, 0.0, 0.0);
   int p1 = prof ? prof->begin(PH_FRONTS, st) : -1;
-  mf_solve(L.mf, Xsub, s, st);
+  run_graph(graph, s, st, [&]() { mf_solve(L.mf, Xsub, s, st); });
   if (prof) prof->end(p1, st, fflops, fbytes);
   int p2 = prof ? prof->begin(PH_RESTRICT, st) : -1;
   if (L.mf.fp32)
@@ -520,22 +571,45 @@ void apply_oras(LevelDev& L, const double2* V, double2* Zout, const double2* Qad
   if (prof) prof->end(p2, st, 0.0, rbytes);
 }
 
-// y_H ~ E^{-1} r_H
+// y_H ~ E^{-1} r_H: a fixed number of right-preconditioned GMRES steps on E
+// with one-level ORAS on the coarse mesh (or the direct factors of E). In the
+// mixed form the whole inner iteration runs on FP32 blocks.
 void coarse_solve(hz_ctx* c, const double2* rH, double2* yH, int s) {
   cudaStream_t st = c->st;
   const int64_t nh = c->cspace.n;
+  LevelDev& L = c->lc;
   if (c->opt.coarse_mode == HZ_COARSE_DIRECT) {
-    apply_oras(c->lc, rH, yH, nullptr, c->XsubH, s, st);
+    apply_oras(L, rH, yH, nullptr, c->XsubH, s, st);
     return;
   }
   DevKrylov& K = c->Kin;
   K.s = s;
-  axpy_cols_zero(yH, nh * s, st);
-  krylov_start(K, rH, st);
   const int64_t vs = nh * s;
+  if (K.fp32) {
+    float2* V = (float2*)K.V;
+    float2* Zk = (float2*)K.Zk;
+    float2* Xs = (float2*)c->XsubH;
+    cast_d2f(rH, c->rH32, vs, st);
+    CK(cudaMemsetAsync(c->yH32, 0, vs * sizeof(float2), st));
+    krylov_start(K, c->rH32, st);
+    for (int j = 0; j < K.m; ++j) {
+      gather_rows_ff(L.mf.gidx, L.sub_rows, V + j * vs, Xs, s, st);
+      mf_solve(L.mf, Xs, s, st);
+      scatter_owned_ff(L.mf.own, L.n, Xs, Zk + j * vs, s, st);
+      spmm_split_f32(c->E, Zk + j * vs, (float2*)K.W, s, st);
+      krylov_arnoldi(K, j, st);
+    }
+    krylov_update(K, c->yH32, st);
+    cast_f2d(c->yH32, yH, vs, st);
+    return;
+  }
+  double2* V = (double2*)K.V;
+  double2* Zk = (double2*)K.Zk;
+  axpy_cols_zero(yH, vs, st);
+  krylov_start(K, rH, st);
   for (int j = 0; j < K.m; ++j) {
-    apply_oras(c->lc, K.V + j * vs, K.Zk + j * vs, nullptr, c->XsubH, s, st);
-    spmm_split(c->E, K.Zk + j * vs, K.W, nullptr, s, 0, st);
+    apply_oras(L, V + j * vs, Zk + j * vs, nullptr, c->XsubH, s, st);
+    spmm_split(c->E, Zk + j * vs, (double2*)K.W, nullptr, s, 0, st);
     krylov_arnoldi(K, j, st);
   }
   krylov_update(K, yH, st);
@@ -559,17 +633,19 @@ void spmm_A(hz_ctx* c, const double2* X, double2* Y, const double2* B, int s, in
 // Zout = M^{-1} V (Eq. 2lvl; Eq. oras without a coarse level)
 void apply_prec(hz_ctx* c, const double2* V, double2* Zout, int s) {
   cudaStream_t st = c->st;
+  GraphCache* gf = c->opt.use_graphs ? &c->g_fronts : nullptr;
   if (!c->has_coarse) {
-    apply_oras(c->lf, V, Zout, nullptr, c->Xsub, s, st, &c->prof);
+    apply_oras(c->lf, V, Zout, nullptr, c->Xsub, s, st, &c->prof, gf);
     return;
   }
   int id = c->prof.begin(PH_COARSE, st);
   spmm_real(c->ZT.n, c->ZT.rp, c->ZT.col, c->ZT.val, V, c->rH, s, st);   // r_H = Z^T v
-  coarse_solve(c, c->rH, c->yH, s);                                       // y_H ~ E^{-1} r_H
+  run_graph(c->opt.use_graphs ? &c->g_coarse : nullptr, s, st,
+            [&]() { coarse_solve(c, c->rH, c->yH, s); });                 // y_H ~ E^{-1} r_H
   spmm_real(c->Z.n, c->Z.rp, c->Z.col, c->Z.val, c->yH, c->Q, s, st);    // q = Z y_H
   c->prof.end(id, st, 0.0, 0.0);
   spmm_A(c, c->Q, c->T, V, s, 1);                                         // t = v - A q
-  apply_oras(c->lf, c->T, Zout, c->Q, c->Xsub, s, st, &c->prof);          // z = M1^{-1} t + q
+  apply_oras(c->lf, c->T, Zout, c->Q, c->Xsub, s, st, &c->prof, gf);      // z = M1^{-1} t + q
 }
 
 // Flexible GMRES on the block c->B (n x s, row-major); solution in c->X.
@@ -597,8 +673,8 @@ int fgmres(hz_ctx* c, int s, hz_stats* stats) {
   while (true) {
     krylov_start(K, c->R, st);
     for (int j = 0; j < m && its < c->opt.maxit; ++j) {
-      apply_prec(c, K.V + j * vs, K.Zk + j * vs, s);
-      spmm_A(c, K.Zk + j * vs, K.W, nullptr, s, 0);
+      apply_prec(c, (double2*)K.V + j * vs, (double2*)K.Zk + j * vs, s);
+      spmm_A(c, (double2*)K.Zk + j * vs, (double2*)K.W, nullptr, s, 0);
       int id = c->prof.begin(PH_ARNOLDI, st);
       krylov_arnoldi(K, j, st);
       // two CGS passes (dots + update) over V_0..j and W, a norm and a scale
@@ -663,6 +739,12 @@ void check_launch() {
   if (e != cudaSuccess) throw CudaFail{e, "kernel launch"};
 }
 
+// order the library stream after the work already queued on the caller's stream
+void join_user(hz_ctx* c) {
+  CK(cudaEventRecord(c->ev_join, c->user_st));
+  CK(cudaStreamWaitEvent(c->st, c->ev_join, 0));
+}
+
 }  // namespace
 
 extern "C" {
@@ -679,6 +761,7 @@ int hz_default_options(hz_options* o) {
   o->leaf_size = 64;
   o->pivot_tau = 1e-12;
   o->verbose = 0;
+  o->use_graphs = 1;
   return HZ_OK;
 }
 
@@ -702,7 +785,6 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
     if (o.coarse_mode < 0 || o.coarse_mode > 2) throw HzError{HZ_EINVAL, "bad coarse_mode"};
     if (o.coarse_mode != HZ_COARSE_NONE && !coarse) throw HzError{HZ_EINVAL, "coarse mesh required"};
     if (o.coarse_mode == HZ_COARSE_GMRES && o.coarse_inner_its < 1) throw HzError{HZ_EINVAL, "coarse_inner_its < 1"};
-    c->st = (cudaStream_t)stream;
     mesh_from_abi(fine, c->fine);
     mesh_build_adjacency(c->fine);
     const int64_t ne = c->fine.ne;
@@ -720,6 +802,10 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
     for (int64_t v : pc)
       if (v == 0) throw HzError{HZ_EINVAL, "empty subdomain in the partition"};
     const double omega = 2.0 * M_PI * freq_hz;
+    c->user_st = (cudaStream_t)stream;
+    CK(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    join_user(c.get());
     c->space = p3_space(c->fine);
     if (c->space.n >= (int64_t)1 << 31) throw HzError{HZ_EINVAL, "more than 2^31 dofs"};
     c->A_host = assemble_global(c->fine, c->space, mvals, omega);
@@ -733,7 +819,7 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
       mesh_from_abi(coarse, c->coarse);
       CoarseSpace C = build_coarse(c->fine, c->space, mvals, part, omega, c->coarse);
       c->cspace = C.space;
-      upload_split(C.E, c->E, c->pool, c->st);
+      upload_split(C.E, c->E, c->pool, c->st, mixed && o.coarse_mode == HZ_COARSE_GMRES);
       upload_real(C.Z, c->Z, c->pool, c->st);
       upload_real(C.ZT, c->ZT, c->pool, c->st);
       if (o.coarse_mode == HZ_COARSE_GMRES) {
@@ -774,8 +860,10 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
   });
   if (rc != HZ_OK) {
     if (c) {
-      cudaStreamSynchronize(c->st);
+      if (c->st) cudaStreamSynchronize(c->st);
       c->pool.release();
+      if (c->st) cudaStreamDestroy(c->st);
+      if (c->ev_join) cudaEventDestroy(c->ev_join);
     }
     return rc;
   }
@@ -885,6 +973,7 @@ static void store_block(hz_ctx* c, const double2* Brow, double* out, int s, int 
 int hz_apply_A(hz_ctx* c, const double* X, double* Y, int32_t s, int32_t on_device) {
   if (!c || !X || !Y || s < 1 || s > c->opt.max_block) return fail(HZ_EINVAL, "bad argument");
   return guarded([&]() -> int {
+    join_user(c);
     ensure_workspace(c, s);
     load_block(c, X, s, on_device);
     spmm_split(c->A, c->B, c->R, nullptr, s, 0, c->st);
@@ -897,6 +986,7 @@ int hz_apply_A(hz_ctx* c, const double* X, double* Y, int32_t s, int32_t on_devi
 int hz_apply_prec(hz_ctx* c, const double* X, double* Y, int32_t s, int32_t on_device) {
   if (!c || !X || !Y || s < 1 || s > c->opt.max_block) return fail(HZ_EINVAL, "bad argument");
   return guarded([&]() -> int {
+    join_user(c);
     ensure_workspace(c, s);
     load_block(c, X, s, on_device);
     apply_prec(c, c->B, c->R, s);
@@ -910,6 +1000,7 @@ int hz_solve_rhs(hz_ctx* c, const double* F, int32_t ns, int32_t F_on_device, do
                  hz_stats* stats) {
   if (!c || !F || !u || ns < 0) return fail(HZ_EINVAL, "bad argument");
   return guarded([&]() -> int {
+    join_user(c);
     const double t0 = now_s();
     const int64_t n = c->space.n;
     int rc = HZ_OK;
@@ -944,6 +1035,7 @@ int hz_solve(hz_ctx* c, const double* src_xyz, const double* src_amp, int32_t ns
              hz_stats* stats) {
   if (!c || !src_xyz || !src_amp || !u || ns < 0) return fail(HZ_EINVAL, "bad argument");
   return guarded([&]() -> int {
+    join_user(c);
     const double t0 = now_s();
     const int64_t n = c->space.n;
     std::vector<int64_t> elem(ns);
@@ -1015,6 +1107,10 @@ void hz_free(hz_ctx* c) {
   if (c->d_srcidx) cudaFree(c->d_srcidx);
   if (c->d_srcval) cudaFree(c->d_srcval);
   c->prof.destroy();
+  c->g_fronts.reset();
+  c->g_coarse.reset();
+  cudaStreamDestroy(c->st);
+  cudaEventDestroy(c->ev_join);
   delete c;
 }
 

@@ -16,6 +16,8 @@ struct DevSplitCsr {
   int64_t* rp_im = nullptr;
   int32_t* col_im = nullptr;
   double* val_im = nullptr;
+  float* val_re_f = nullptr;  // FP32 copies (mixed-form coarse operator only)
+  float* val_im_f = nullptr;
 };
 
 // Multifrontal factors of a batch of local matrices, grouped by tree height.
@@ -78,12 +80,14 @@ void scatter_owned_f32(const int* own, int64_t n, const float2* Xsub, const doub
                        cudaStream_t st);
 
 // --- Krylov (one Krylov space per column) ---
+// Vector-typed arrays hold double2 (fp32 = 0) or float2 (fp32 = 1); the
+// Hessenberg data, rotations and norms are FP64 in both cases.
 struct DevKrylov {
-  int m = 0, s = 0;
+  int m = 0, s = 0, fp32 = 0;
   int64_t n = 0;
-  double2* V = nullptr;     // [(m+1)][n][s]
-  double2* Zk = nullptr;    // [m][n][s]
-  double2* W = nullptr;     // [n][s]
+  void* V = nullptr;        // [(m+1)][n][s]
+  void* Zk = nullptr;       // [m][n][s]
+  void* W = nullptr;        // [n][s]
   double2* H = nullptr;     // [s][(m+1) m] Hessenberg, rotated in place
   double2* hpart = nullptr; // partial dot products [nblk][m+1][s]
   double2* h1 = nullptr;    // [m+1][s]
@@ -100,11 +104,18 @@ struct DevKrylov {
   int nblk = 0;
 };
 
-void column_norms(const double2* X, int64_t n, int s, double* out, DevKrylov& K, cudaStream_t st);
-void krylov_start(DevKrylov& K, const double2* R, cudaStream_t st);  // V0 = R/beta, g = beta e1, flags
-void krylov_arnoldi(DevKrylov& K, int j, cudaStream_t st);           // CGS2 of W against V_0..j, H, Givens
-void krylov_update(DevKrylov& K, double2* X, cudaStream_t st);        // X += Zk y
+void column_norms(const void* X, int64_t n, int s, double* out, DevKrylov& K, cudaStream_t st);
+void krylov_start(DevKrylov& K, const void* R, cudaStream_t st);  // V0 = R/beta, g = beta e1, flags
+void krylov_arnoldi(DevKrylov& K, int j, cudaStream_t st);         // CGS2 of W against V_0..j, H, Givens
+void krylov_update(DevKrylov& K, void* X, cudaStream_t st);        // X += Zk y
 void axpy_cols_zero(double2* X, int64_t count, cudaStream_t st);
+
+// --- FP32 coarse level (mixed form) ---
+void spmm_split_f32(const DevSplitCsr& A, const float2* X, float2* Y, int s, cudaStream_t st);
+void gather_rows_ff(const int* idx, int64_t nrows, const float2* X, float2* Y, int s, cudaStream_t st);
+void scatter_owned_ff(const int* own, int64_t n, const float2* Xsub, float2* Z, int s, cudaStream_t st);
+void cast_d2f(const double2* X, float2* Y, int64_t count, cudaStream_t st);
+void cast_f2d(const float2* X, double2* Y, int64_t count, cudaStream_t st);
 
 // --- right-hand sides / layout ---
 void scatter_point_sources(double2* B, int64_t n, int s, const int* idx, const double2* val, int nent,

@@ -15,8 +15,9 @@
 //   forward  (leaves to root): t = X_t b_P;  y_P = t[0:k] / D;
 //                              parent update  w = c_U + t[k:f]
 //   backward (root to leaves): x_P = X_t^T [y_P; x_U]
-// so that both sweeps are tiled matrix products over 64-row tiles spread
-// over all SMs, in FP64 or (mixed form) in FP32.
+// so that both sweeps are streaming matrix products (forward: one thread per
+// factor row; backward: one warp per pivot column) spread over all SMs, in
+// FP64 or (mixed form) in FP32.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -218,9 +219,8 @@ void mf_factor(DevMF& mf, double tau_abs, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // Solve sweeps
 // ---------------------------------------------------------------------------
-constexpr int TM = 64;   // rows (forward) / pivots (backward) per tile
-constexpr int TK = 16;   // reduction chunk
-constexpr int NT = 256;  // threads per tile: TM rows x 4 column groups
+constexpr int FWD_ROWS = 128;  // rows per forward tile: one thread per row
+constexpr int BWD_COLS = 8;    // pivots per backward tile: one warp per pivot
 
 // front vector: Win[0:k] = Xsub[pivots], Win[k:f] = 0, plus the children's
 // update vectors (Wout[k_c:f_c] of each child) added at their parent rows
@@ -252,64 +252,60 @@ __global__ void k_mf_fvec(const int* __restrict__ list, const int* __restrict__ 
   }
 }
 
-// forward tile: rows [r0, r0+TM) of t = X_t b_P
-template <typename V, int CPT>
-__global__ void __launch_bounds__(NT) k_mf_fwd_gemm(const int2* __restrict__ tiles, const int* __restrict__ kk,
-                                                    const int* __restrict__ ff, const int64_t* __restrict__ rowoff,
-                                                    const int64_t* __restrict__ Moff,
-                                                    const int64_t* __restrict__ Doff, const int* __restrict__ rows,
-                                                    const V* __restrict__ M, const V* __restrict__ Dinv,
-                                                    const V* __restrict__ Win, V* __restrict__ Wout, int s) {
-  __shared__ V Ms[TK][TM];
-  __shared__ V Bs[TK][64];
+// Forward tile: rows [r0, r0 + FWD_ROWS) of t = X_t b_P. One thread per row
+// streams its row of X_t (consecutive threads read consecutive addresses of
+// the column-major factor) against chunks of b_P staged in shared memory;
+// the s right-hand sides are register accumulators, so every factor entry
+// is read from HBM once per sweep.
+template <typename V, int S>
+__global__ void __launch_bounds__(FWD_ROWS) k_mf_fwd(const int2* __restrict__ tiles, const int* __restrict__ kk,
+                                                     const int* __restrict__ ff, const int64_t* __restrict__ rowoff,
+                                                     const int64_t* __restrict__ Moff, const int64_t* __restrict__ Doff,
+                                                     const V* __restrict__ M, const V* __restrict__ Dinv,
+                                                     const V* __restrict__ Win, V* __restrict__ Wout, int s) {
+  constexpr int KC = (S >= 32) ? 32 : 64;
+  __shared__ V bs[KC][S];
   const int2 tile = tiles[blockIdx.x];
   const int t = tile.x, r0 = tile.y;
   const int f = ff[t], k = kk[t];
-  const V* Mt = M + Moff[t];
-  const V* bin = Win + rowoff[t] * s;
-  const int r = threadIdx.x % TM, cg = threadIdx.x / TM;
-  const int kend = (r0 < k) ? min(k, r0 + TM) : k;
-  V acc[CPT];
+  const int r = r0 + threadIdx.x;
+  const bool active = r < f;
+  const V* Mr = M + Moff[t] + r;
+  const int64_t ro = rowoff[t];
+  const V* bin = Win + ro * s;
+  const int kend = (r0 < k) ? min(k, r0 + FWD_ROWS) : k;
+  V acc[S];
 #pragma unroll
-  for (int q = 0; q < CPT; ++q) acc[q] = mk2((decltype(V::x))0, (decltype(V::x))0);
-  for (int k0 = 0; k0 < kend; k0 += TK) {
-    for (int i = threadIdx.x; i < TK * TM; i += NT) {
-      int l = i / TM, rr = i % TM;
-      int gr = r0 + rr, gc = k0 + l;
-      Ms[l][rr] = (gr < f && gc < kend) ? Mt[gr + (int64_t)gc * f] : mk2((decltype(V::x))0, (decltype(V::x))0);
-    }
-    for (int i = threadIdx.x; i < TK * s; i += NT) {
-      int l = i / s, c = i % s;
-      Bs[l][c] = (k0 + l < kend) ? bin[(k0 + l) * s + c] : mk2((decltype(V::x))0, (decltype(V::x))0);
+  for (int c = 0; c < S; ++c) acc[c] = mk2((decltype(V::x))0, (decltype(V::x))0);
+  for (int k0 = 0; k0 < kend; k0 += KC) {
+    const int lmax = min(KC, kend - k0);
+    for (int i = threadIdx.x; i < KC * S; i += FWD_ROWS) {
+      int l = i / S, c = i % S;
+      bs[l][c] = (l < lmax && c < s) ? bin[(k0 + l) * s + c] : mk2((decltype(V::x))0, (decltype(V::x))0);
     }
     __syncthreads();
+    if (active) {
+#pragma unroll 4
+      for (int l = 0; l < lmax; ++l) {
+        const V m = Mr[(int64_t)(k0 + l) * f];
 #pragma unroll
-    for (int l = 0; l < TK; ++l) {
-      V m = Ms[l][r];
-#pragma unroll
-      for (int q = 0; q < CPT; ++q) {
-        int c = cg + 4 * q;
-        if (c < s) acc[q] = c_fma(m, Bs[l][c], acc[q]);
+        for (int c = 0; c < S; ++c) acc[c] = c_fma(m, bs[l][c], acc[c]);
       }
     }
     __syncthreads();
   }
-  const int gr = r0 + r;
-  if (gr >= f) return;
-  const int64_t ro = rowoff[t];
-  if (gr < k) {
-    V di = Dinv[Doff[t] + gr];
+  if (!active) return;
+  V* out = Wout + (ro + r) * s;
+  if (r < k) {
+    const V di = Dinv[Doff[t] + r];
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) {
-      int c = cg + 4 * q;
-      if (c < s) Wout[(ro + gr) * s + c] = c_mul(acc[q], di);
-    }
+    for (int c = 0; c < S; ++c)
+      if (c < s) out[c] = c_mul(acc[c], di);
   } else {
+    const V* in = bin + (int64_t)r * s;
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) {
-      int c = cg + 4 * q;
-      if (c < s) Wout[(ro + gr) * s + c] = c_add(bin[gr * s + c], acc[q]);
-    }
+    for (int c = 0; c < S; ++c)
+      if (c < s) out[c] = c_add(in[c], acc[c]);
   }
 }
 
@@ -328,60 +324,65 @@ __global__ void k_mf_bvec(const int* __restrict__ list, const int* __restrict__ 
   }
 }
 
-// backward tile: pivots [j0, j0+TM) of x_P = X_t^T [y_P; x_U]
-template <typename V, int CPT>
-__global__ void __launch_bounds__(NT) k_mf_bwd_gemm(const int2* __restrict__ tiles, const int* __restrict__ kk,
-                                                    const int* __restrict__ ff, const int64_t* __restrict__ rowoff,
-                                                    const int64_t* __restrict__ Moff, const int* __restrict__ rows,
-                                                    const V* __restrict__ M, const V* __restrict__ Win,
-                                                    const V* __restrict__ Wout, V* __restrict__ Xsub, int s) {
-  __shared__ V Ms[TK][TM + 1];
-  __shared__ V Bs[TK][64];
+// Backward tile: pivots [j0, j0 + BWD_COLS) of x_P = X_t^T [y_P; x_U]. One
+// warp per pivot column j: the lanes stream column j of X_t (contiguous)
+// against chunks of the front vector staged in shared memory, then reduce.
+template <typename V, int S>
+__global__ void __launch_bounds__(32 * BWD_COLS) k_mf_bwd(const int2* __restrict__ tiles, const int* __restrict__ kk,
+                                                          const int* __restrict__ ff,
+                                                          const int64_t* __restrict__ rowoff,
+                                                          const int64_t* __restrict__ Moff, const int* __restrict__ rows,
+                                                          const V* __restrict__ M, const V* __restrict__ Win,
+                                                          const V* __restrict__ Wout, V* __restrict__ Xsub, int s) {
+  constexpr int RC = (S >= 32) ? 32 : 64;
+  __shared__ V vs[RC][S + 1];
   const int2 tile = tiles[blockIdx.x];
   const int t = tile.x, j0 = tile.y;
   const int f = ff[t], k = kk[t];
-  const V* Mt = M + Moff[t];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j = j0 + w;
   const int64_t ro = rowoff[t];
-  const int j = threadIdx.x % TM, cg = threadIdx.x / TM;
-  V acc[CPT];
+  const V* Mj = M + Moff[t] + (int64_t)j * f;
+  V acc[S];
 #pragma unroll
-  for (int q = 0; q < CPT; ++q) acc[q] = mk2((decltype(V::x))0, (decltype(V::x))0);
-  for (int r0 = j0; r0 < f; r0 += TK) {
-    for (int i = threadIdx.x; i < TK * TM; i += NT) {
-      int l = i % TK, jj = i / TK;  // consecutive threads walk down a column
-      int gr = r0 + l, gc = j0 + jj;
-      Ms[l][jj] = (gr < f && gc < k) ? Mt[gr + (int64_t)gc * f] : mk2((decltype(V::x))0, (decltype(V::x))0);
-    }
-    for (int i = threadIdx.x; i < TK * s; i += NT) {
-      int l = i / s, c = i % s;
-      int gr = r0 + l;
+  for (int c = 0; c < S; ++c) acc[c] = mk2((decltype(V::x))0, (decltype(V::x))0);
+  for (int r0 = j0; r0 < f; r0 += RC) {
+    const int lmax = min(RC, f - r0);
+    for (int i = threadIdx.x; i < RC * S; i += 32 * BWD_COLS) {
+      int l = i / S, c = i % S;
       V v = mk2((decltype(V::x))0, (decltype(V::x))0);
-      if (gr < f) v = gr < k ? Wout[(ro + gr) * s + c] : Win[(ro + gr) * s + c];
-      Bs[l][c] = v;
+      if (l < lmax && c < s) {
+        const int gr = r0 + l;
+        v = gr < k ? Wout[(ro + gr) * s + c] : Win[(ro + gr) * s + c];
+      }
+      vs[l][c] = v;
     }
     __syncthreads();
+    if (j < k) {
+      for (int l = lane; l < lmax; l += 32) {
+        const int gr = r0 + l;
+        if (gr < j) continue;  // X_t is zero above the diagonal of its pivot block
+        const V m = Mj[gr];
 #pragma unroll
-    for (int l = 0; l < TK; ++l) {
-      V m = Ms[l][j];
-#pragma unroll
-      for (int q = 0; q < CPT; ++q) {
-        int c = cg + 4 * q;
-        if (c < s) acc[q] = c_fma(m, Bs[l][c], acc[q]);
+        for (int c = 0; c < S; ++c) acc[c] = c_fma(m, vs[l][c], acc[c]);
       }
     }
     __syncthreads();
   }
-  const int gj = j0 + j;
-  if (gj >= k) return;
-  const int xr = rows[ro + gj];
+  if (j >= k) return;
 #pragma unroll
-  for (int q = 0; q < CPT; ++q) {
-    int c = cg + 4 * q;
-    if (c < s) Xsub[(int64_t)xr * s + c] = acc[q];
-  }
+  for (int c = 0; c < S; ++c)
+    for (int o = 16; o > 0; o >>= 1) {
+      acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, o);
+      acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, o);
+    }
+  V* xo = Xsub + (int64_t)rows[ro + j] * s;
+#pragma unroll
+  for (int c = 0; c < S; ++c)
+    if (c < s && c % 32 == lane) xo[c] = acc[c];
 }
 
-template <typename V, int CPT>
+template <typename V, int S>
 static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
   V* Win = (V*)mf.Win;
   V* Wout = (V*)mf.Wout;
@@ -394,8 +395,8 @@ static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
                                         mf.child_idx, Xsub, Win, Wout, s);
     int tb = mf.ftile_ptr_h[l], te = mf.ftile_ptr_h[l + 1];
     if (te > tb)
-      k_mf_fwd_gemm<V, CPT><<<te - tb, NT, 0, st>>>(mf.ftiles + tb, mf.k, mf.f, mf.rowoff, mf.Moff, mf.Doff, mf.rows,
-                                                    M, Dv, Win, Wout, s);
+      k_mf_fwd<V, S><<<te - tb, FWD_ROWS, 0, st>>>(mf.ftiles + tb, mf.k, mf.f, mf.rowoff, mf.Moff, mf.Doff, M, Dv,
+                                                   Win, Wout, s);
   }
   for (int l = mf.nlevels - 1; l >= 0; --l) {
     int b = mf.level_ptr_h[l], e = mf.level_ptr_h[l + 1];
@@ -403,23 +404,27 @@ static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
     k_mf_bvec<V><<<e - b, 256, 0, st>>>(mf.level_list + b, mf.k, mf.f, mf.rowoff, mf.rows, Xsub, Win, s);
     int tb = mf.btile_ptr_h[l], te = mf.btile_ptr_h[l + 1];
     if (te > tb)
-      k_mf_bwd_gemm<V, CPT><<<te - tb, NT, 0, st>>>(mf.btiles + tb, mf.k, mf.f, mf.rowoff, mf.Moff, mf.rows, M, Win,
-                                                    Wout, Xsub, s);
+      k_mf_bwd<V, S><<<te - tb, 32 * BWD_COLS, 0, st>>>(mf.btiles + tb, mf.k, mf.f, mf.rowoff, mf.Moff, mf.rows, M,
+                                                        Win, Wout, Xsub, s);
   }
 }
 
 template <typename V>
 static void solve_dispatch(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
-  if (s <= 4)
+  if (s <= 1)
     solve_impl<V, 1>(mf, Xsub, s, st);
-  else if (s <= 8)
+  else if (s <= 2)
     solve_impl<V, 2>(mf, Xsub, s, st);
-  else if (s <= 16)
+  else if (s <= 4)
     solve_impl<V, 4>(mf, Xsub, s, st);
-  else if (s <= 32)
+  else if (s <= 8)
     solve_impl<V, 8>(mf, Xsub, s, st);
-  else
+  else if (s <= 16)
     solve_impl<V, 16>(mf, Xsub, s, st);
+  else if (s <= 32)
+    solve_impl<V, 32>(mf, Xsub, s, st);
+  else
+    solve_impl<V, 64>(mf, Xsub, s, st);
 }
 
 void mf_solve(DevMF& mf, void* Xsub, int s, cudaStream_t st) {

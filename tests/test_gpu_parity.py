@@ -128,3 +128,34 @@ def test_solve_rhs_plane_wave_data():
         perm = dof_perm(S, space, 1000.0)
         u, st = S.solve_rhs(F[perm][None, :])
         assert rel_l2(u[0], u_or[perm]) <= 1e-8
+
+
+@pytest.mark.parametrize("coarse", [hz.HZ_COARSE_NONE, hz.HZ_COARSE_GMRES])
+def test_mixed_form_wavefield_matches_oracle(cube, coarse):
+    """Mixed form (complex FP32 local solves inside FP64 FGMRES): the
+    wavefield still converges to the FP64 oracle's discrete solution; at
+    rtol 1e-6 the error bound of the mixed form is 1e-5."""
+    p, T = cube
+    space, A, F = oa.system(p["fine"], p["velocity"], p["freq"], p["src_xyz"])
+    u_or = oa.solve(A, F)
+    for rtol, bound in ((1e-6, 1e-5), (1e-10, 1e-8)):
+        with hz.Solver.from_problem(p, rtol=rtol, precision=hz.HZ_PREC_MIXED, coarse_mode=coarse) as S:
+            perm = dof_perm(S, space, 1000.0)
+            u, st = S.solve(p["src_xyz"])
+            err = rel_l2(u, u_or[:, perm])
+            print("mixed rtol", rtol, "iterations", st["iterations"], "rel L2", err)
+            assert st["converged"] == 1
+            assert err.max() <= bound
+
+
+def test_graphs_and_eager_agree(cube):
+    """The captured-graph replay of the local and coarse solves gives the
+    same preconditioner as eager launches."""
+    p, _ = cube
+    X = wl.random_rhs(6859, 3, 9)
+    with hz.Solver.from_problem(p, use_graphs=1) as S1, hz.Solver.from_problem(p, use_graphs=0) as S0:
+        Y1 = S1.apply_prec(X)
+        Y1b = S1.apply_prec(X)
+        Y0 = S0.apply_prec(X)
+    np.testing.assert_array_equal(Y1, Y1b)
+    np.testing.assert_array_equal(Y1, Y0)
