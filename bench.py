@@ -46,12 +46,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=["overthrust5", "cube"], default="overthrust5")
+    ap.add_argument("--config", choices=["overthrust5", "overthrust5_quarter", "cube"], default="overthrust5",
+                    help="overthrust5_quarter: the 10 x 10 km corner of the same model (profiling case)")
     ap.add_argument("--forms", default="mixed,fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the FP64 form")
     ap.add_argument("--fp64-warmup", type=int, default=1, help="warm-up steps of the FP64 form")
     ap.add_argument("--variants", default="one_level", help="extra preconditioner variants of the headline form")
+    ap.add_argument("--maxit", type=int, default=500, help="FGMRES iteration cap (lower it only for profiling runs)")
+    ap.add_argument("--coarse", choices=["gmres", "none", "direct"], default="gmres",
+                    help="coarse level of the headline forms (the paper's: gmres, 10 inner steps)")
     return ap.parse_args()
 
 
@@ -69,6 +73,12 @@ def problem(cfg):
 
     if cfg == "cube":
         return wl.cube_problem(), "cube 1 km, 6^3 cells, P3 (6859 dofs), 2 Hz, 4 subdomains, 1 source"
+    if cfg == "overthrust5_quarter":
+        p = wl.overthrust_problem(5.0, nparts=16, seed=0, crop=(0.5, 0.5, 1.0),
+                                  sources=wl.surface_source_grid(4, 4, 1250.0, 8750.0))
+        nx, ny, nz = p["fine"]["ncells"]
+        return p, ("Overthrust-like 5 Hz, 10x10 km corner crop, %dx%dx%d cells, 16 subdomains, %d sources"
+                   % (nx, ny, nz, len(p["src_xyz"])))
     p = wl.overthrust_problem(5.0, nparts=64, seed=0)
     nx, ny, nz = p["fine"]["ncells"]
     return p, ("Overthrust-like 20x20x4.65 km, 5 Hz, %dx%dx%d cells x 6 Kuhn tets, P3, 64 subdomains "
@@ -143,12 +153,14 @@ def barrier(ws):
 
 
 def max_over_ranks(x, ws):
+    """Largest value over the ranks (the slowest rank's time)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -197,36 +209,39 @@ def run_reference(args):
 def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, **opts):
     prec = hz.HZ_PREC_MIXED if form == "mixed" else hz.HZ_PREC_FP64
     t0 = time.time()
-    S = hz.Solver.from_problem(prob, precision=prec, rtol=1e-6, stream=stream, **opts)
+    S = hz.Solver.from_problem(prob, precision=prec, rtol=1e-6, stream=stream, maxit=MAXIT, **opts)
     setup_wall = time.time() - t0
     info = S.info()
     src = prob["src_xyz"]
     ns = len(src)
     out = torch.empty((ns, S.n), dtype=torch.complex128, device="cuda")
     iters = []
+    notconv = MAXIT < 500
     for _ in range(warmup):
-        _, st = S.solve(src, out=out)
+        _, st = S.solve(src, out=out, raise_on_notconv=not notconv)
         iters.append(st["iterations"])
     barrier(ws)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    launches0 = S.info()["kernel_launches"]
     S.profile_begin()
     e0.record(stream)
     stats = []
     for _ in range(steps):
-        _, st = S.solve(src, out=out)
+        _, st = S.solve(src, out=out, raise_on_notconv=not notconv)
         stats.append(st)
     e1.record(stream)
     torch.cuda.synchronize()
     prof = S.profile_end()
+    launches = S.info()["kernel_launches"] - launches0
     barrier(ws)
     ms = e0.elapsed_time(e1)
     ms = max_over_ranks(ms, ws)
     res = {"rhs_per_s": ns * steps * ws / (ms / 1e3), "ms_per_step": ms / steps, "steps": steps, "warmup": warmup,
            "iterations": [s["iterations"] for s in stats], "max_rel_residual": max(s["max_rel_residual"] for s in stats),
            "converged": all(s["converged"] for s in stats), "setup_s": setup_wall,
-           "factor_s": stats[0]["factor_seconds"], "info": info, "phases": prof}
+           "factor_s": stats[0]["factor_seconds"], "info": info, "phases": prof, "gpu_launches": launches}
     if with_e2e:
         import numpy as np
 
@@ -235,7 +250,7 @@ def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, **o
         torch.cuda.synchronize()
         t = time.perf_counter()
         for _ in range(steps):
-            S.solve(src, out=hostbuf)
+            S.solve(src, out=hostbuf, raise_on_notconv=not notconv)
         torch.cuda.synchronize()
         el = max_over_ranks(time.perf_counter() - t, ws)
         res["e2e"] = {"value": ns * steps * ws / el, "unit": "RHS/s",
@@ -245,8 +260,13 @@ def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, **o
     return res
 
 
+MAXIT = 500
+
+
 def main():
+    global MAXIT
     args = parse()
+    MAXIT = args.maxit
     if args.impl == "reference":
         run_reference(args)
         return
@@ -271,7 +291,9 @@ def main():
         warm = args.warmup if form != "fp64" else args.fp64_warmup
         if i == 0:
             clocks.start()
-        results[form] = measure_form(prob, form, steps, warm, stream, ws, torch, hz, with_e2e=(i == 0))
+        cm = {"gmres": hz.HZ_COARSE_GMRES, "none": hz.HZ_COARSE_NONE, "direct": hz.HZ_COARSE_DIRECT}[args.coarse]
+        results[form] = measure_form(prob, form, steps, warm, stream, ws, torch, hz, with_e2e=(i == 0),
+                                     coarse_mode=cm)
         if i == 0:
             clk = clocks.stop()
     variants = {}
@@ -306,7 +328,7 @@ def main():
                    (r["info"]["device_bytes"] / 1e9), "parallelism": "replicas x%d (sources)" % ws},
         "roofline": roof,
         "clocks": clk,
-        "gpu_launches": None,
+        "gpu_launches": r["gpu_launches"],
         "e2e": r.get("e2e"),
         "forms": {f: {k: v for k, v in results[f].items() if k not in ("info",)} for f in results},
     }

@@ -119,6 +119,8 @@ typedef struct hz_info {
   int32_t nlevels;          /* tree heights (fine) */
   int32_t perturbed_pivots; /* static perturbations applied in the factorisations */
   double device_bytes;      /* device memory held by the context */
+  int64_t kernel_launches;  /* kernels launched by the library in this process so far (kernels of
+                               replayed CUDA graphs included) */
 } hz_info;
 
 /* Fills *opt with the defaults listed above. */
@@ -172,7 +174,8 @@ int hz_apply_prec(hz_ctx* ctx, const double* X, double* Y, int32_t s, int32_t on
  * (products with A), "fronts" (fine-level local solves), "restrict_prolong"
  * (fine R_i gathers and partition-of-unity scatters), "coarse" (Z^T, the
  * coarse solve and Z), "arnoldi" (outer orthogonalisation, least squares and
- * solution update). flops and bytes are the algorithmic counts of the
+ * solution update), "precond_spmm" (the residual t = v - A q inside M^{-1},
+ * FP32 in the mixed form). flops and bytes are the algorithmic counts of the
  * recorded calls (complex multiply-add = 8 flops; bytes = compulsory
  * traffic: matrix/factor entries, indices and the input/output blocks). */
 typedef struct hz_phase_time {

@@ -84,15 +84,16 @@ struct DevPool {
 struct MFHost {
   int64_t factor_entries = 0, front_entries = 0, stored_entries = 0;
   int max_front = 0, nfronts = 0, nlevels = 0;
-  std::vector<int> level_ptr, ftile_ptr, btile_ptr;
+  std::vector<int> level_ptr, ftile_ptr, btile_ptr, frb_ptr, brb_ptr;
+  std::vector<int64_t> level_row;
   // per-level algorithmic work of one solve sweep (complex multiply-adds per column)
   std::vector<double> fwd_cmacs, bwd_cmacs;
 };
 
 // Pack the fronts of several local matrices into one device structure;
 // sub_off[i] is the first row of subdomain i in the flat sub-vector.
-constexpr int MF_FWD_ROWS = 128;  // rows per forward tile (k_mf_fwd)
-constexpr int MF_BWD_COLS = 8;    // pivots per backward tile (k_mf_bwd)
+constexpr int MF_TILE_ROWS = 128;  // output rows per sweep tile (MF_TILE in mf.cu)
+constexpr int MF_TILE_K = 128;     // reduction length per sweep tile (MF_TK in mf.cu)
 
 void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const FrontTree*>& trees,
               const std::vector<int64_t>& sub_off, bool fp32, DevMF& mf, MFHost& info, DevPool& pool,
@@ -113,9 +114,30 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
       info.factor_entries += (int64_t)T.k[t] * (T.k[t] + 1) / 2 + (int64_t)T.k[t] * T.m[t];
     }
   }
+  // level schedule by tree height; front rows are laid out level by level so
+  // that every level's rows form one contiguous range
+  int maxh = 0;
+  for (int g = 0; g < nf; ++g) maxh = std::max(maxh, height[g]);
+  info.nlevels = maxh + 1;
+  info.nfronts = nf;
+  info.level_ptr.assign(maxh + 2, 0);
+  for (int g = 0; g < nf; ++g) info.level_ptr[height[g] + 1]++;
+  for (int l = 0; l <= maxh; ++l) info.level_ptr[l + 1] += info.level_ptr[l];
+  std::vector<int> level_list(nf);
+  {
+    std::vector<int> fill(info.level_ptr.begin(), info.level_ptr.end() - 1);
+    for (int g = 0; g < nf; ++g) level_list[fill[height[g]]++] = g;
+  }
+  {
+    int64_t acc = 0;
+    for (int q = 0; q < nf; ++q) {
+      rowoff[level_list[q]] = acc;
+      acc += f[level_list[q]];
+    }
+    rowoff[nf] = acc;
+  }
   for (int g = 0; g < nf; ++g) {
     Foff[g + 1] = Foff[g] + (int64_t)f[g] * f[g];
-    rowoff[g + 1] = rowoff[g] + f[g];
     Moff[g + 1] = Moff[g] + (int64_t)f[g] * k[g];
     Doff[g + 1] = Doff[g] + k[g];
     info.max_front = std::max(info.max_front, f[g]);
@@ -180,36 +202,84 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
       amap_ptr[g + 1] = (int64_t)amap_pos.size();
     }
   }
-  // level schedule by tree height
-  int maxh = 0;
-  for (int g = 0; g < nf; ++g) maxh = std::max(maxh, height[g]);
-  info.nlevels = maxh + 1;
-  info.nfronts = nf;
-  info.level_ptr.assign(maxh + 2, 0);
-  for (int g = 0; g < nf; ++g) info.level_ptr[height[g] + 1]++;
-  for (int l = 0; l <= maxh; ++l) info.level_ptr[l + 1] += info.level_ptr[l];
-  std::vector<int> level_list(nf);
-  {
-    std::vector<int> fill(info.level_ptr.begin(), info.level_ptr.end() - 1);
-    for (int g = 0; g < nf; ++g) level_list[fill[height[g]]++] = g;
+  // per-row front id and local position; extend-add sources of every row
+  std::vector<int> row_front(rowoff[nf]), row_local(rowoff[nf]);
+  for (int g = 0; g < nf; ++g)
+    for (int r = 0; r < f[g]; ++r) {
+      row_front[rowoff[g] + r] = g;
+      row_local[rowoff[g] + r] = r;
+    }
+  std::vector<std::pair<int64_t, int64_t>> contrib;  // (parent row, child update row), child-list order
+  for (int g = 0; g < nf; ++g)
+    for (int q = child_ptr[g]; q < child_ptr[g + 1]; ++q) {
+      const int ch = child_idx[q];
+      for (int a = 0; a < f[ch] - k[ch]; ++a) {
+        const int64_t cr = rowoff[ch] + k[ch] + a;
+        contrib.push_back({rowoff[g] + cmap[cr], cr});
+      }
+    }
+  std::stable_sort(contrib.begin(), contrib.end(),
+                   [](const std::pair<int64_t, int64_t>& x, const std::pair<int64_t, int64_t>& y) {
+                     return x.first < y.first;
+                   });
+  std::vector<int64_t> cptr(rowoff[nf] + 1, 0);
+  std::vector<int> cidx(contrib.size());
+  for (size_t q = 0; q < contrib.size(); ++q) {
+    cptr[contrib[q].first + 1]++;
+    cidx[q] = (int)contrib[q].second;
   }
-  // solve tiles: forward over the f rows, backward over the k pivots
-  std::vector<int2> ftiles, btiles;
+  for (int64_t r = 0; r < rowoff[nf]; ++r) cptr[r + 1] += cptr[r];
+  // sweep tiles: (front, first output row, first reduction index, partial slot)
+  // and row blocks (front, first output row, tiles, first slot); slots restart
+  // at 0 on every level
+  std::vector<int4> ftiles, frb, btiles, brb;
   info.ftile_ptr.assign(1, 0);
   info.btile_ptr.assign(1, 0);
+  info.frb_ptr.assign(1, 0);
+  info.brb_ptr.assign(1, 0);
   info.fwd_cmacs.assign(maxh + 1, 0.0);
   info.bwd_cmacs.assign(maxh + 1, 0.0);
+  int64_t max_slots = 1;
   for (int l = 0; l <= maxh; ++l) {
+    int fslot = 0, bslot = 0;
     for (int q = info.level_ptr[l]; q < info.level_ptr[l + 1]; ++q) {
       const int g = level_list[q];
-      for (int r0 = 0; r0 < f[g]; r0 += MF_FWD_ROWS) ftiles.push_back(make_int2(g, r0));
-      for (int j0 = 0; j0 < k[g]; j0 += MF_BWD_COLS) btiles.push_back(make_int2(g, j0));
+      // a row block covered by a single tile finishes inside the tile (slot
+      // -1); the others sum their partial tiles in k_mf_reduce
+      for (int r0 = 0; r0 < f[g]; r0 += MF_TILE_ROWS) {
+        const int kend = r0 < k[g] ? std::min(k[g], r0 + MF_TILE_ROWS) : k[g];
+        const int nk = (kend + MF_TILE_K - 1) / MF_TILE_K;
+        if (nk == 1) {
+          ftiles.push_back(make_int4(g, r0, 0, -1));
+          continue;
+        }
+        frb.push_back(make_int4(g, r0, nk, fslot));
+        for (int c0 = 0; c0 < kend; c0 += MF_TILE_K) ftiles.push_back(make_int4(g, r0, c0, fslot++));
+      }
+      for (int j0 = 0; j0 < k[g]; j0 += MF_TILE_ROWS) {
+        const int nk = (f[g] - j0 + MF_TILE_K - 1) / MF_TILE_K;
+        if (nk == 1) {
+          btiles.push_back(make_int4(g, j0, j0, -1));
+          continue;
+        }
+        brb.push_back(make_int4(g, j0, nk, bslot));
+        for (int c0 = j0; c0 < f[g]; c0 += MF_TILE_K) btiles.push_back(make_int4(g, j0, c0, bslot++));
+      }
       const double kk = k[g], mm = f[g] - k[g];
       info.fwd_cmacs[l] += kk * (kk + 1) / 2 + kk * mm;
       info.bwd_cmacs[l] += kk * (kk + 1) / 2 + kk * mm;
     }
+    max_slots = std::max<int64_t>(max_slots, std::max(fslot, bslot));
     info.ftile_ptr.push_back((int)ftiles.size());
     info.btile_ptr.push_back((int)btiles.size());
+    info.frb_ptr.push_back((int)frb.size());
+    info.brb_ptr.push_back((int)brb.size());
+  }
+  info.level_row.assign(maxh + 2, 0);
+  for (int l = 0; l <= maxh; ++l) {
+    int64_t e = info.level_row[l];
+    for (int q = info.level_ptr[l]; q < info.level_ptr[l + 1]; ++q) e += f[level_list[q]];
+    info.level_row[l + 1] = e;
   }
   mf.nfronts = nf;
   mf.nlevels = info.nlevels;
@@ -220,6 +290,16 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
   mf.level_ptr_h = info.level_ptr.data();
   mf.ftile_ptr_h = info.ftile_ptr.data();
   mf.btile_ptr_h = info.btile_ptr.data();
+  mf.frb_ptr_h = info.frb_ptr.data();
+  mf.brb_ptr_h = info.brb_ptr.data();
+  mf.level_row_h = info.level_row.data();
+  mf.max_slots = max_slots;
+  mf.frb = pool.upload(frb, st);
+  mf.brb = pool.upload(brb, st);
+  mf.row_front = pool.upload(row_front, st);
+  mf.row_local = pool.upload(row_local, st);
+  mf.cptr = pool.upload(cptr, st);
+  mf.cidx = pool.upload(cidx, st);
   mf.fp32 = fp32 ? 1 : 0;
   mf.M_total = Moff[nf];
   mf.D_total = Doff[nf];
@@ -229,6 +309,7 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
   mf.Doff = pool.upload(Doff, st);
   const size_t esz = fp32 ? sizeof(float2) : sizeof(double2);
   mf.M = pool.alloc<char>(Moff[nf] * esz);
+  mf.MT = pool.alloc<char>(Moff[nf] * esz);
   mf.Dinv = pool.alloc<char>(Doff[nf] * esz);
   mf.level_list = pool.upload(level_list, st);
   mf.k = pool.upload(k, st);
@@ -273,12 +354,17 @@ struct DevReal {
   int64_t* rp = nullptr;
   int32_t* col = nullptr;
   double* val = nullptr;
+  float* val_f = nullptr;  // FP32 copy (mixed form)
 };
-void upload_real(const CsrR& A, DevReal& D, DevPool& pool, cudaStream_t st) {
+void upload_real(const CsrR& A, DevReal& D, DevPool& pool, cudaStream_t st, bool with_f32 = false) {
   D.n = A.nrows;
   D.rp = pool.upload(A.rowptr, st);
   D.col = pool.upload(A.col, st);
   D.val = pool.upload(A.val, st);
+  if (with_f32) {
+    std::vector<float> vf(A.val.begin(), A.val.end());
+    D.val_f = pool.upload(vf, st);
+  }
 }
 
 struct LevelDev {             // one level of ORAS on the device
@@ -354,8 +440,9 @@ void mesh_from_abi(const hz_mesh* in, Mesh& m) {
 
 }  // namespace
 
-enum Phase { PH_SPMM = 0, PH_FRONTS, PH_RESTRICT, PH_COARSE, PH_ARNOLDI, PH_COUNT };
-static const char* PHASE_NAMES[PH_COUNT] = {"spmm_A", "fronts", "restrict_prolong", "coarse", "arnoldi"};
+enum Phase { PH_SPMM = 0, PH_FRONTS, PH_RESTRICT, PH_COARSE, PH_ARNOLDI, PH_PSPMM, PH_COUNT };
+static const char* PHASE_NAMES[PH_COUNT] = {"spmm_A", "fronts", "restrict_prolong", "coarse", "arnoldi",
+                                            "precond_spmm"};
 
 // CUDA-event timing of hot-path phases (off unless hz_profile_begin)
 struct Profiler {
@@ -399,6 +486,7 @@ struct Profiler {
 // block width or the workspace changes.
 struct GraphCache {
   int s = -1;
+  long long kernels = 0;  // kernel launches recorded in the graph
   cudaGraphExec_t exec = nullptr;
   void reset() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -433,6 +521,7 @@ struct hz_ctx {
   double2 *B = nullptr, *X = nullptr, *R = nullptr, *T = nullptr, *Q = nullptr, *Xsub = nullptr, *U = nullptr;
   double2 *rH = nullptr, *yH = nullptr, *XsubH = nullptr;
   float2 *rH32 = nullptr, *yH32 = nullptr;
+  float2 *v32 = nullptr, *q32 = nullptr, *t32 = nullptr;  // FP32 preconditioner blocks (mixed form)
   DevKrylov Kout, Kin;
   double* bnorm = nullptr;
   double* rnorm = nullptr;
@@ -468,6 +557,7 @@ void alloc_krylov(DevKrylov& K, int64_t n, int s, int m, DevPool& p, bool fp32) 
   K.tol = p.alloc<double>(s);
   K.kc = p.alloc<int>(s);
   K.done = p.alloc<int>(s);
+  K.reorth = p.alloc<int>(s);
 }
 
 void ensure_workspace(hz_ctx* c, int s) {
@@ -495,8 +585,8 @@ void ensure_workspace(hz_ctx* c, int s) {
   c->U = p.alloc<double2>(n * s);
   const size_t ef = c->lf.mf.fp32 ? sizeof(float2) : sizeof(double2);
   c->Xsub = (double2*)p.alloc<char>(c->lf.sub_rows * s * ef);
-  c->lf.mf.Win = p.alloc<char>(c->lf.mf.rows_total * s * ef);
   c->lf.mf.Wout = p.alloc<char>(c->lf.mf.rows_total * s * ef);
+  c->lf.mf.P = p.alloc<char>((size_t)c->lf.mf.max_slots * MF_TILE_ROWS * s * ef);
   c->lf.mf.s_cap = s;
   alloc_krylov(c->Kout, n, s, c->opt.restart, p, false);
   if (c->has_coarse) {
@@ -505,8 +595,8 @@ void ensure_workspace(hz_ctx* c, int s) {
     c->yH = p.alloc<double2>(nh * s);
     const size_t ec = c->lc.mf.fp32 ? sizeof(float2) : sizeof(double2);
     c->XsubH = (double2*)p.alloc<char>(c->lc.sub_rows * s * ec);
-    c->lc.mf.Win = p.alloc<char>(c->lc.mf.rows_total * s * ec);
     c->lc.mf.Wout = p.alloc<char>(c->lc.mf.rows_total * s * ec);
+    c->lc.mf.P = p.alloc<char>((size_t)c->lc.mf.max_slots * MF_TILE_ROWS * s * ec);
     c->lc.mf.s_cap = s;
     if (c->opt.coarse_mode == HZ_COARSE_GMRES) {
       alloc_krylov(c->Kin, nh, s, std::max(1, c->opt.coarse_inner_its), p, c->lc.mf.fp32 != 0);
@@ -515,6 +605,9 @@ void ensure_workspace(hz_ctx* c, int s) {
     if (c->lc.mf.fp32) {
       c->rH32 = p.alloc<float2>(nh * s);
       c->yH32 = p.alloc<float2>(nh * s);
+      c->v32 = p.alloc<float2>(n * s);
+      c->q32 = p.alloc<float2>(n * s);
+      c->t32 = p.alloc<float2>(n * s);
     }
   }
   c->bnorm = p.alloc<double>(s);
@@ -534,15 +627,19 @@ void run_graph(GraphCache* g, int s, cudaStream_t st, F&& body) {
   if (g->s != s || !g->exec) {
     g->reset();
     cudaGraph_t graph;
+    const long long before = g_kernel_launches.load();
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     body();
     CK(cudaStreamEndCapture(st, &graph));
+    g->kernels = g_kernel_launches.load() - before;
+    count_launch(-g->kernels);  // captured, not executed
     cudaError_t e = cudaGraphInstantiate(&g->exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) throw CudaFail{e, "cudaGraphInstantiate"};
     g->s = s;
   }
   CK(cudaGraphLaunch(g->exec, st));
+  count_launch(g->kernels);
 }
 
 // ORAS on one level: Z = sum_i R_i^T D_i A_i^{-1} R_i V (+ Qadd)
@@ -589,7 +686,7 @@ void coarse_solve(hz_ctx* c, const double2* rH, double2* yH, int s) {
     float2* V = (float2*)K.V;
     float2* Zk = (float2*)K.Zk;
     float2* Xs = (float2*)c->XsubH;
-    cast_d2f(rH, c->rH32, vs, st);
+    if (rH) cast_d2f(rH, c->rH32, vs, st);
     CK(cudaMemsetAsync(c->yH32, 0, vs * sizeof(float2), st));
     krylov_start(K, c->rH32, st);
     for (int j = 0; j < K.m; ++j) {
@@ -600,7 +697,7 @@ void coarse_solve(hz_ctx* c, const double2* rH, double2* yH, int s) {
       krylov_arnoldi(K, j, st);
     }
     krylov_update(K, c->yH32, st);
-    cast_f2d(c->yH32, yH, vs, st);
+    if (yH) cast_f2d(c->yH32, yH, vs, st);
     return;
   }
   double2* V = (double2*)K.V;
@@ -636,6 +733,33 @@ void apply_prec(hz_ctx* c, const double2* V, double2* Zout, int s) {
   GraphCache* gf = c->opt.use_graphs ? &c->g_fronts : nullptr;
   if (!c->has_coarse) {
     apply_oras(c->lf, V, Zout, nullptr, c->Xsub, s, st, &c->prof, gf);
+    return;
+  }
+  if (c->lf.mf.fp32 && c->v32 && c->opt.coarse_mode == HZ_COARSE_GMRES) {
+    // mixed form: the whole of M^{-1} on FP32 blocks, z returned in FP64
+    const int64_t n = c->space.n;
+    int id = c->prof.begin(PH_COARSE, st);
+    cast_d2f(V, c->v32, n * s, st);
+    spmm_real_f32(c->ZT.n, c->ZT.rp, c->ZT.col, c->ZT.val_f, c->v32, c->rH32, s, st);  // r_H = Z^T v
+    run_graph(c->opt.use_graphs ? &c->g_coarse : nullptr, s, st,
+              [&]() { coarse_solve(c, nullptr, nullptr, s); });                         // y_H ~ E^{-1} r_H
+    spmm_real_f32(c->Z.n, c->Z.rp, c->Z.col, c->Z.val_f, c->yH32, c->q32, s, st);      // q = Z y_H
+    c->prof.end(id, st, 0.0, 0.0);
+    int ip = c->prof.begin(PH_PSPMM, st);
+    spmm_split_f32(c->A, c->q32, c->t32, s, st, c->v32);                               // t = v - A q
+    c->prof.end(ip, st, 4.0 * (c->A.nnz_re + c->A.nnz_im) * s,
+                6.0 * (c->A.nnz_re + c->A.nnz_im) + 16.0 * (n + 1) + 24.0 * n * s);
+    LevelDev& L = c->lf;
+    int p0 = c->prof.begin(PH_RESTRICT, st);
+    gather_rows_ff(L.mf.gidx, L.sub_rows, c->t32, (float2*)c->Xsub, s, st);
+    c->prof.end(p0, st, 0.0, 0.0);
+    int p1 = c->prof.begin(PH_FRONTS, st);
+    run_graph(gf, s, st, [&]() { mf_solve(L.mf, c->Xsub, s, st); });
+    c->prof.end(p1, st, 8.0 * s * 2.0 * L.info.factor_entries,
+                8.0 * 2.0 * L.info.factor_entries + 2.0 * 8.0 * s * L.sub_rows);
+    int p2 = c->prof.begin(PH_RESTRICT, st);
+    scatter_owned_fq(L.mf.own, L.n, (const float2*)c->Xsub, c->q32, Zout, s, st);     // z = M1^{-1} t + q
+    c->prof.end(p2, st, 0.0, 4.0 * L.sub_rows + 16.0 * L.sub_rows * s + 4.0 * L.n + 32.0 * L.n * s);
     return;
   }
   int id = c->prof.begin(PH_COARSE, st);
@@ -809,8 +933,8 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
     c->space = p3_space(c->fine);
     if (c->space.n >= (int64_t)1 << 31) throw HzError{HZ_EINVAL, "more than 2^31 dofs"};
     c->A_host = assemble_global(c->fine, c->space, mvals, omega);
-    upload_split(c->A_host, c->A, c->pool, c->st);
     const bool mixed = o.precision == HZ_PREC_MIXED;
+    upload_split(c->A_host, c->A, c->pool, c->st, mixed);
     std::vector<Subdomain> subs = build_subdomains(c->fine, c->space, part, nparts, mvals, omega);
     build_level(c->space, subs, o.leaf_size, mixed, c->lf, c->pool, c->st);
     subs.clear();
@@ -820,8 +944,8 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
       CoarseSpace C = build_coarse(c->fine, c->space, mvals, part, omega, c->coarse);
       c->cspace = C.space;
       upload_split(C.E, c->E, c->pool, c->st, mixed && o.coarse_mode == HZ_COARSE_GMRES);
-      upload_real(C.Z, c->Z, c->pool, c->st);
-      upload_real(C.ZT, c->ZT, c->pool, c->st);
+      upload_real(C.Z, c->Z, c->pool, c->st, mixed);
+      upload_real(C.ZT, c->ZT, c->pool, c->st, mixed);
       if (o.coarse_mode == HZ_COARSE_GMRES) {
         std::vector<Subdomain> csubs = build_subdomains(c->coarse, c->cspace, C.part, nparts, C.mvals, omega);
         build_level(c->cspace, csubs, o.leaf_size, mixed, c->lc, c->pool, c->st);
@@ -901,6 +1025,7 @@ int hz_get_info(const hz_ctx* c, hz_info* info) {
   info->nlevels = c->lf.info.nlevels;
   info->perturbed_pivots = c->perturbed;
   info->device_bytes = c->pool.bytes + c->work.bytes;
+  info->kernel_launches = g_kernel_launches.load();
   return HZ_OK;
 }
 

@@ -17,6 +17,8 @@
 
 namespace hz {
 
+std::atomic<long long> g_kernel_launches{0};
+
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
@@ -78,8 +80,8 @@ void spmm_split(const DevSplitCsr& A, const double2* X, double2* Y, const double
                 cudaStream_t st) {
   int64_t work = A.n * s;
   if (work == 0) return;
-  k_spmm_split<<<grid_for(work, 256), 256, 0, st>>>(A.n, s, A.rp_re, A.col_re, A.val_re, A.rp_im, A.col_im,
-                                                    A.val_im, X, Y, B, mode);
+  { k_spmm_split<<<grid_for(work, 256), 256, 0, st>>>(A.n, s, A.rp_re, A.col_re, A.val_re, A.rp_im, A.col_im,
+                                                    A.val_im, X, Y, B, mode); count_launch(); }
 }
 
 __global__ void k_spmm_real(int64_t n, int s, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
@@ -102,7 +104,7 @@ void spmm_real(int64_t nrows, const int64_t* rp, const int32_t* col, const doubl
                double2* Y, int s, cudaStream_t st) {
   int64_t work = nrows * s;
   if (work == 0) return;
-  k_spmm_real<<<grid_for(work, 256), 256, 0, st>>>(nrows, s, rp, col, val, X, Y);
+  { k_spmm_real<<<grid_for(work, 256), 256, 0, st>>>(nrows, s, rp, col, val, X, Y); count_launch(); }
 }
 
 // ---------------------------------------------------------------------------
@@ -120,7 +122,7 @@ __global__ void k_gather_rows(const int* __restrict__ idx, int64_t nrows, const 
 
 void gather_rows(const int* idx, int64_t nrows, const double2* X, double2* Y, int s, cudaStream_t st) {
   if (nrows * s == 0) return;
-  k_gather_rows<<<grid_for(nrows * s, 256), 256, 0, st>>>(idx, nrows, X, Y, s);
+  { k_gather_rows<<<grid_for(nrows * s, 256), 256, 0, st>>>(idx, nrows, X, Y, s); count_launch(); }
 }
 
 __global__ void k_scatter_owned(const int* __restrict__ own, int64_t n, const double2* __restrict__ Xsub,
@@ -137,7 +139,7 @@ __global__ void k_scatter_owned(const int* __restrict__ own, int64_t n, const do
 void scatter_owned(const int* own, int64_t n, const double2* Xsub, const double2* Q, double2* Z, int s,
                    cudaStream_t st) {
   if (n * s == 0) return;
-  k_scatter_owned<<<grid_for(n * s, 256), 256, 0, st>>>(own, n, Xsub, Q, Z, s);
+  { k_scatter_owned<<<grid_for(n * s, 256), 256, 0, st>>>(own, n, Xsub, Q, Z, s); count_launch(); }
 }
 
 __global__ void k_zero(double2* X, int64_t count) {
@@ -145,7 +147,7 @@ __global__ void k_zero(double2* X, int64_t count) {
   if (g < count) X[g] = make_double2(0.0, 0.0);
 }
 void axpy_cols_zero(double2* X, int64_t count, cudaStream_t st) {
-  if (count) k_zero<<<grid_for(count, 256), 256, 0, st>>>(X, count);
+  if (count) { k_zero<<<grid_for(count, 256), 256, 0, st>>>(X, count); count_launch(); }
 }
 
 // ---------------------------------------------------------------------------
@@ -159,7 +161,7 @@ void scatter_point_sources(double2* B, int64_t n, int s, const int* idx, const d
                            cudaStream_t st) {
   (void)n;
   (void)s;
-  if (nent) k_point_sources<<<grid_for(nent, 128), 128, 0, st>>>(B, idx, val, nent);
+  if (nent) { k_point_sources<<<grid_for(nent, 128), 128, 0, st>>>(B, idx, val, nent); count_launch(); }
 }
 
 __global__ void k_to_rows(const double2* __restrict__ F, double2* __restrict__ B, int64_t n, int s) {
@@ -177,10 +179,10 @@ __global__ void k_from_rows(const double2* __restrict__ B, double2* __restrict__
   F[g] = B[r * s + c];
 }
 void transpose_to_rows(const double2* F, double2* B, int64_t n, int s, cudaStream_t st) {
-  if (n * s) k_to_rows<<<grid_for(n * s, 256), 256, 0, st>>>(F, B, n, s);
+  if (n * s) { k_to_rows<<<grid_for(n * s, 256), 256, 0, st>>>(F, B, n, s); count_launch(); }
 }
 void transpose_from_rows(const double2* B, double2* F, int64_t n, int s, cudaStream_t st) {
-  if (n * s) k_from_rows<<<grid_for(n * s, 256), 256, 0, st>>>(B, F, n, s);
+  if (n * s) { k_from_rows<<<grid_for(n * s, 256), 256, 0, st>>>(B, F, n, s); count_launch(); }
 }
 
 __global__ void k_copy(const double2* __restrict__ X, double2* __restrict__ Y, int64_t count) {
@@ -188,7 +190,7 @@ __global__ void k_copy(const double2* __restrict__ X, double2* __restrict__ Y, i
   if (g < count) Y[g] = X[g];
 }
 void cast_copy(const double2* X, double2* Y, int64_t count, cudaStream_t st) {
-  if (count) k_copy<<<grid_for(count, 256), 256, 0, st>>>(X, Y, count);
+  if (count) { k_copy<<<grid_for(count, 256), 256, 0, st>>>(X, Y, count); count_launch(); }
 }
 
 }  // namespace hz

@@ -2,9 +2,16 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <cstdint>
 
 namespace hz {
+
+// Kernel launches issued by the library (graph replays add the kernels of
+// the replayed graph); read through hz_get_info.
+extern std::atomic<long long> g_kernel_launches;
+inline void count_launch(long long n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // Split complex CSR: A = A_re + i A_im, A_im holding only the entries with a
 // nonzero imaginary part (Robin faces); both share the row count.
@@ -32,8 +39,19 @@ struct DevMF {
   int* ftile_ptr_h = nullptr;   // host [nlevels+1] forward tiles per level
   int* btile_ptr_h = nullptr;   // host [nlevels+1] backward tiles per level
   int* level_list = nullptr;    // device [nfronts] front ids ordered by height
-  int2* ftiles = nullptr;       // (front, first row) of every forward tile
-  int2* btiles = nullptr;       // (front, first pivot) of every backward tile
+  int* frb_ptr_h = nullptr;     // host [nlevels+1] forward row blocks per level
+  int* brb_ptr_h = nullptr;     // host [nlevels+1] backward row blocks per level
+  int64_t* level_row_h = nullptr;  // host [nlevels+1] first front row of each level
+  int64_t max_slots = 0;        // partial-result slots of the largest level
+  int4* ftiles = nullptr;       // forward tiles (front, first row, first column, slot)
+  int4* btiles = nullptr;       // backward tiles (front, first pivot, first row, slot)
+  int4* frb = nullptr;          // forward row blocks (front, first row, tiles, first slot)
+  int4* brb = nullptr;          // backward row blocks
+  int* row_front = nullptr;     // [rows_total] front of each front row
+  int* row_local = nullptr;     // [rows_total] position inside its front
+  int64_t* cptr = nullptr;      // [rows_total+1] extend-add sources of each front row
+  int* cidx = nullptr;          // child update rows, in child order
+  void* P = nullptr;            // partial tile results [max_slots][128][s_cap]
   int* k = nullptr;             // pivots per front
   int* f = nullptr;             // front order k + m
   int64_t* Foff = nullptr;      // offset of the f x f front workspace (column-major)
@@ -49,10 +67,10 @@ struct DevMF {
   int64_t* amap_val = nullptr;  // index into Aval
   double2* Aval = nullptr;      // concatenated local matrix values
   double2* F = nullptr;         // factorisation workspace (freed after setup)
-  void* M = nullptr;            // X_t factors (double2 or float2)
+  void* M = nullptr;            // X_t factors (double2 or float2), column-major f x k
+  void* MT = nullptr;           // X_t^T, column-major k x f (backward sweep)
   void* Dinv = nullptr;         // 1/D (double2 or float2)
-  void* Win = nullptr;          // front vectors [rows_total][s_cap]
-  void* Wout = nullptr;
+  void* Wout = nullptr;         // front vectors [rows_total][s_cap]: y_P and parent updates
   int s_cap = 0;
   int* gidx = nullptr;          // [nsub_rows] global row of each sub-vector row (R_i)
   int* own = nullptr;           // [n] sub-vector row of the owning copy (D_i Boolean)
@@ -101,17 +119,23 @@ struct DevKrylov {
   double* tol = nullptr;    // [s] absolute stop tolerance per column
   int* kc = nullptr;        // [s] accepted Arnoldi steps
   int* done = nullptr;      // [s]
+  int* reorth = nullptr;    // [s] second Gram-Schmidt pass needed
   int nblk = 0;
 };
 
 void column_norms(const void* X, int64_t n, int s, double* out, DevKrylov& K, cudaStream_t st);
 void krylov_start(DevKrylov& K, const void* R, cudaStream_t st);  // V0 = R/beta, g = beta e1, flags
-void krylov_arnoldi(DevKrylov& K, int j, cudaStream_t st);         // CGS2 of W against V_0..j, H, Givens
+void krylov_arnoldi(DevKrylov& K, int j, cudaStream_t st);         // CGS (+selective 2nd pass), H, Givens
 void krylov_update(DevKrylov& K, void* X, cudaStream_t st);        // X += Zk y
 void axpy_cols_zero(double2* X, int64_t count, cudaStream_t st);
 
 // --- FP32 coarse level (mixed form) ---
-void spmm_split_f32(const DevSplitCsr& A, const float2* X, float2* Y, int s, cudaStream_t st);
+void spmm_split_f32(const DevSplitCsr& A, const float2* X, float2* Y, int s, cudaStream_t st,
+                    const float2* B = nullptr);  // Y = A X, or B - A X
+void spmm_real_f32(int64_t nrows, const int64_t* rp, const int32_t* col, const float* val, const float2* X,
+                   float2* Y, int s, cudaStream_t st);
+void scatter_owned_fq(const int* own, int64_t n, const float2* Xsub, const float2* Q, double2* Z, int s,
+                      cudaStream_t st);
 void gather_rows_ff(const int* idx, int64_t nrows, const float2* X, float2* Y, int s, cudaStream_t st);
 void scatter_owned_ff(const int* own, int64_t n, const float2* Xsub, float2* Z, int s, cudaStream_t st);
 void cast_d2f(const double2* X, float2* Y, int64_t count, cudaStream_t st);

@@ -62,9 +62,11 @@ constexpr int KBLOCK = 256;
 }  // namespace
 
 // part[blk][i0+q][c] = sum over the block's rows of conj(V_{i0+q}[r][c]) W[r][c]
+// (columns with mask[c] == 0 contribute zeros without reading their data)
 template <typename V>
 __global__ void k_mdot(const V* __restrict__ Vb, int64_t vstride, int i0, int ni, const V* __restrict__ W, int64_t n,
-                       int s, int64_t rows_per_blk, double2* __restrict__ part, int mstride) {
+                       int s, int64_t rows_per_blk, double2* __restrict__ part, int mstride,
+                       const int* __restrict__ mask) {
   __shared__ double2 sh[KBLOCK];
   const int nrl = blockDim.x / s;
   const int c = threadIdx.x % s, rl = threadIdx.x / s;
@@ -72,7 +74,7 @@ __global__ void k_mdot(const V* __restrict__ Vb, int64_t vstride, int i0, int ni
 #pragma unroll
   for (int q = 0; q < IG; ++q) acc[q] = zero<V>();
   const int64_t r0 = blockIdx.x * rows_per_blk;
-  const int64_t r1 = min(n, r0 + rows_per_blk);
+  const int64_t r1 = (mask && !mask[c]) ? r0 : min(n, r0 + rows_per_blk);
   for (int64_t r = r0 + rl; r < r1; r += nrl) {
     const V w = W[r * s + c];
 #pragma unroll
@@ -91,34 +93,43 @@ __global__ void k_mdot(const V* __restrict__ Vb, int64_t vstride, int i0, int ni
   }
 }
 
-// out[i][c] = sum over blocks of part[blk][i][c] (fixed order)
+// out[i][c] = sum over blocks of part[blk][i][c]: one warp per (i, c), lanes
+// stride over the blocks, fixed shuffle tree (deterministic)
 __global__ void k_reduce_part(const double2* __restrict__ part, int nblk, int ni, int s, int mstride,
                               double2* __restrict__ out) {
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= ni * s) return;
-  int i = g / s, c = g % s;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= ni * s) return;
+  const int i = w / s, c = w % s;
   double2 a = make_double2(0.0, 0.0);
-  for (int b = 0; b < nblk; ++b) a = zadd(a, part[((int64_t)b * mstride + i) * s + c]);
-  out[i * s + c] = a;
+  for (int b = lane; b < nblk; b += 32) a = zadd(a, part[((int64_t)b * mstride + i) * s + c]);
+  for (int o = 16; o > 0; o >>= 1) {
+    a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
+    a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+  }
+  if (lane == 0) out[i * s + c] = a;
 }
 
 template <typename V>
-static void mdot(DevKrylov& K, const V* Vb, int64_t vstride, int ni, const V* W, double2* out, cudaStream_t st) {
+static void mdot(DevKrylov& K, const V* Vb, int64_t vstride, int ni, const V* W, double2* out, cudaStream_t st,
+                 const int* mask = nullptr) {
   const int s = K.s;
   const int block = (KBLOCK / s) * s;
   const int64_t rpb = (K.n + K.nblk - 1) / K.nblk;
   for (int i0 = 0; i0 < ni; i0 += IG)
-    k_mdot<V><<<K.nblk, block, 0, st>>>(Vb, vstride, i0, std::min(IG, ni - i0), W, K.n, s, rpb, K.hpart, K.m + 1);
-  k_reduce_part<<<grid_for((int64_t)ni * s, 128), 128, 0, st>>>(K.hpart, K.nblk, ni, s, K.m + 1, out);
+    { k_mdot<V><<<K.nblk, block, 0, st>>>(Vb, vstride, i0, std::min(IG, ni - i0), W, K.n, s, rpb, K.hpart, K.m + 1,
+                                        mask); count_launch(); }
+  { k_reduce_part<<<grid_for((int64_t)ni * s * 32, 256), 256, 0, st>>>(K.hpart, K.nblk, ni, s, K.m + 1, out); count_launch(); }
 }
 
 // W[r][c] -= sum_{i<ni} V_i[r][c] h[i][c]
 template <typename V>
 __global__ void k_update(const V* __restrict__ Vb, int64_t vstride, int ni, const double2* __restrict__ h,
-                         V* __restrict__ W, int64_t n, int s) {
+                         V* __restrict__ W, int64_t n, int s, const int* __restrict__ mask) {
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n * s) return;
   int c = (int)(g % s);
+  if (mask && !mask[c]) return;
   V w = W[g];
   for (int i = 0; i < ni; ++i) w = cfms(Vb[i * vstride + g], from2<V>(h[i * s + c]), w);
   W[g] = w;
@@ -132,6 +143,19 @@ __global__ void k_scale_cols(const V* __restrict__ X, const double* __restrict__
   const auto a = (decltype(V::x))sc[g % s];
   V x = X[g];
   Y[g] = mk(a * x.x, a * x.y);
+}
+
+// Second Gram-Schmidt pass only where the first one cancelled: with w the
+// vector before and w' after the first pass, ||w'||^2 = ||w||^2 - sum |h_i|^2;
+// reorthogonalise when ||w'||^2 < ||w||^2 / 2 ("twice is enough" criterion).
+__global__ void k_reorth_flags(int s, int j, const double2* __restrict__ h1, const double2* __restrict__ w2,
+                               int* __restrict__ flags) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= s) return;
+  double hh = 0.0;
+  for (int i = 0; i <= j; ++i) hh += zabs2(h1[i * s + c]);
+  const double ww = w2[c].x;
+  flags[c] = (ww - hh < 0.5 * ww) ? 1 : 0;
 }
 
 __global__ void k_norm_finish(const double2* __restrict__ nrm2, int s, double* __restrict__ out) {
@@ -241,14 +265,14 @@ __global__ void k_sol_update(const V* __restrict__ Zk, int64_t vstride, const do
 template <typename V>
 static void column_norms_t(const V* X, int64_t n, int s, double* out, DevKrylov& K, cudaStream_t st) {
   mdot<V>(K, X, 0, 1, X, K.h2, st);
-  k_norm_finish<<<1, 64, 0, st>>>(K.h2, s, out);
+  { k_norm_finish<<<1, 64, 0, st>>>(K.h2, s, out); count_launch(); }
 }
 
 template <typename V>
 static void krylov_start_t(DevKrylov& K, const V* R, cudaStream_t st) {
   mdot<V>(K, R, 0, 1, R, K.h2, st);
-  k_start<<<1, 64, 0, st>>>(K.s, K.m, K.h2, K.tol, K.g, K.beta, K.kc, K.done, K.res);
-  k_scale_cols<V><<<grid_for(K.n * K.s, 256), 256, 0, st>>>(R, K.beta, (V*)K.V, K.n, K.s);
+  { k_start<<<1, 64, 0, st>>>(K.s, K.m, K.h2, K.tol, K.g, K.beta, K.kc, K.done, K.res); count_launch(); }
+  { k_scale_cols<V><<<grid_for(K.n * K.s, 256), 256, 0, st>>>(R, K.beta, (V*)K.V, K.n, K.s); count_launch(); }
 }
 
 template <typename V>
@@ -257,21 +281,23 @@ static void krylov_arnoldi_t(DevKrylov& K, int j, cudaStream_t st) {
   const unsigned gr = grid_for(vs, 256);
   V* Vb = (V*)K.V;
   V* W = (V*)K.W;
-  mdot<V>(K, Vb, vs, j + 1, W, K.h1, st);
-  k_update<V><<<gr, 256, 0, st>>>(Vb, vs, j + 1, K.h1, W, K.n, K.s);
-  mdot<V>(K, Vb, vs, j + 1, W, K.h2, st);
-  k_update<V><<<gr, 256, 0, st>>>(Vb, vs, j + 1, K.h2, W, K.n, K.s);
   double2* nrm = K.h2 + (int64_t)K.m * K.s;  // row m of h2: scratch for |W|^2
   mdot<V>(K, W, 0, 1, W, nrm, st);
-  k_arnoldi_finish<<<1, 64, 0, st>>>(K.s, K.m, j, K.h1, K.h2, nrm, K.H, K.cs, K.sn, K.g, K.beta, K.tol, K.kc, K.done,
-                                     K.res);
-  k_scale_cols<V><<<gr, 256, 0, st>>>(W, K.beta, Vb + (int64_t)(j + 1) * vs, K.n, K.s);
+  mdot<V>(K, Vb, vs, j + 1, W, K.h1, st);
+  { k_update<V><<<gr, 256, 0, st>>>(Vb, vs, j + 1, K.h1, W, K.n, K.s, nullptr); count_launch(); }
+  { k_reorth_flags<<<1, 64, 0, st>>>(K.s, j, K.h1, nrm, K.reorth); count_launch(); }
+  mdot<V>(K, Vb, vs, j + 1, W, K.h2, st, K.reorth);
+  { k_update<V><<<gr, 256, 0, st>>>(Vb, vs, j + 1, K.h2, W, K.n, K.s, K.reorth); count_launch(); }
+  mdot<V>(K, W, 0, 1, W, nrm, st);
+  { k_arnoldi_finish<<<1, 64, 0, st>>>(K.s, K.m, j, K.h1, K.h2, nrm, K.H, K.cs, K.sn, K.g, K.beta, K.tol, K.kc, K.done,
+                                     K.res); count_launch(); }
+  { k_scale_cols<V><<<gr, 256, 0, st>>>(W, K.beta, Vb + (int64_t)(j + 1) * vs, K.n, K.s); count_launch(); }
 }
 
 template <typename V>
 static void krylov_update_t(DevKrylov& K, V* X, cudaStream_t st) {
-  k_ls_solve<<<1, 64, 0, st>>>(K.s, K.m, K.H, K.g, K.kc, K.y);
-  k_sol_update<V><<<grid_for(K.n * K.s, 256), 256, 0, st>>>((const V*)K.Zk, K.n * K.s, K.y, K.kc, X, K.n, K.s, K.m);
+  { k_ls_solve<<<1, 64, 0, st>>>(K.s, K.m, K.H, K.g, K.kc, K.y); count_launch(); }
+  { k_sol_update<V><<<grid_for(K.n * K.s, 256), 256, 0, st>>>((const V*)K.Zk, K.n * K.s, K.y, K.kc, X, K.n, K.s, K.m); count_launch(); }
 }
 
 void column_norms(const void* X, int64_t n, int s, double* out, DevKrylov& K, cudaStream_t st) {
@@ -303,10 +329,11 @@ void krylov_update(DevKrylov& K, void* X, cudaStream_t st) {
 // FP32 coarse-level helpers (mixed form): SpMM with float values, gathers
 // and scatters between FP32 blocks, precision casts
 // ---------------------------------------------------------------------------
+// Y = A X, or Y = B - A X when B is given (FP32 values and blocks)
 __global__ void k_spmm_split_f32(int64_t n, int s, const int64_t* __restrict__ rp_re, const int32_t* __restrict__ col_re,
                                  const float* __restrict__ val_re, const int64_t* __restrict__ rp_im,
                                  const int32_t* __restrict__ col_im, const float* __restrict__ val_im,
-                                 const float2* __restrict__ X, float2* __restrict__ Y) {
+                                 const float2* __restrict__ X, float2* __restrict__ Y, const float2* __restrict__ B) {
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t r = g / s;
   int c = (int)(g - r * s);
@@ -324,14 +351,55 @@ __global__ void k_spmm_split_f32(int64_t n, int s, const int64_t* __restrict__ r
     ar = fmaf(-b, x.y, ar);
     ai = fmaf(b, x.x, ai);
   }
+  if (B) {
+    const float2 b = B[g];
+    Y[g] = make_float2(b.x - ar, b.y - ai);
+  } else {
+    Y[g] = make_float2(ar, ai);
+  }
+}
+
+void spmm_split_f32(const DevSplitCsr& A, const float2* X, float2* Y, int s, cudaStream_t st, const float2* B) {
+  int64_t work = A.n * s;
+  if (work == 0) return;
+  { k_spmm_split_f32<<<grid_for(work, 256), 256, 0, st>>>(A.n, s, A.rp_re, A.col_re, A.val_re_f, A.rp_im, A.col_im,
+                                                        A.val_im_f, X, Y, B); count_launch(); }
+}
+
+__global__ void k_spmm_real_f32(int64_t n, int s, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                const float* __restrict__ val, const float2* __restrict__ X, float2* __restrict__ Y) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t r = g / s;
+  int c = (int)(g - r * s);
+  if (r >= n) return;
+  float ar = 0.f, ai = 0.f;
+  for (int64_t p = rp[r], pe = rp[r + 1]; p < pe; ++p) {
+    float a = val[p];
+    float2 x = X[(int64_t)col[p] * s + c];
+    ar = fmaf(a, x.x, ar);
+    ai = fmaf(a, x.y, ai);
+  }
   Y[g] = make_float2(ar, ai);
 }
 
-void spmm_split_f32(const DevSplitCsr& A, const float2* X, float2* Y, int s, cudaStream_t st) {
-  int64_t work = A.n * s;
-  if (work == 0) return;
-  k_spmm_split_f32<<<grid_for(work, 256), 256, 0, st>>>(A.n, s, A.rp_re, A.col_re, A.val_re_f, A.rp_im, A.col_im,
-                                                        A.val_im_f, X, Y);
+void spmm_real_f32(int64_t nrows, const int64_t* rp, const int32_t* col, const float* val, const float2* X,
+                   float2* Y, int s, cudaStream_t st) {
+  if (nrows * s) { k_spmm_real_f32<<<grid_for(nrows * s, 256), 256, 0, st>>>(nrows, s, rp, col, val, X, Y); count_launch(); }
+}
+
+// z = (FP64) Xsub[owning copy] + (FP64) q  (prolongation of the FP32 local solutions)
+__global__ void k_scatter_owned_fq(const int* __restrict__ own, int64_t n, const float2* __restrict__ Xsub,
+                                   const float2* __restrict__ Q, double2* __restrict__ Z, int s) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t r = g / s;
+  if (r >= n) return;
+  const float2 v = Xsub[(int64_t)own[r] * s + (g - r * s)];
+  const float2 q = Q[g];
+  Z[g] = make_double2((double)v.x + (double)q.x, (double)v.y + (double)q.y);
+}
+void scatter_owned_fq(const int* own, int64_t n, const float2* Xsub, const float2* Q, double2* Z, int s,
+                      cudaStream_t st) {
+  if (n * s) { k_scatter_owned_fq<<<grid_for(n * s, 256), 256, 0, st>>>(own, n, Xsub, Q, Z, s); count_launch(); }
 }
 
 __global__ void k_gather_ff(const int* __restrict__ idx, int64_t nrows, const float2* __restrict__ X,
@@ -342,7 +410,7 @@ __global__ void k_gather_ff(const int* __restrict__ idx, int64_t nrows, const fl
   Y[g] = X[(int64_t)idx[r] * s + (g - r * s)];
 }
 void gather_rows_ff(const int* idx, int64_t nrows, const float2* X, float2* Y, int s, cudaStream_t st) {
-  if (nrows * s) k_gather_ff<<<grid_for(nrows * s, 256), 256, 0, st>>>(idx, nrows, X, Y, s);
+  if (nrows * s) { k_gather_ff<<<grid_for(nrows * s, 256), 256, 0, st>>>(idx, nrows, X, Y, s); count_launch(); }
 }
 
 __global__ void k_scatter_ff(const int* __restrict__ own, int64_t n, const float2* __restrict__ Xsub,
@@ -353,7 +421,7 @@ __global__ void k_scatter_ff(const int* __restrict__ own, int64_t n, const float
   Z[g] = Xsub[(int64_t)own[r] * s + (g - r * s)];
 }
 void scatter_owned_ff(const int* own, int64_t n, const float2* Xsub, float2* Z, int s, cudaStream_t st) {
-  if (n * s) k_scatter_ff<<<grid_for(n * s, 256), 256, 0, st>>>(own, n, Xsub, Z, s);
+  if (n * s) { k_scatter_ff<<<grid_for(n * s, 256), 256, 0, st>>>(own, n, Xsub, Z, s); count_launch(); }
 }
 
 __global__ void k_d2f(const double2* __restrict__ X, float2* __restrict__ Y, int64_t count) {
@@ -365,10 +433,10 @@ __global__ void k_f2d(const float2* __restrict__ X, double2* __restrict__ Y, int
   if (g < count) Y[g] = make_double2(X[g].x, X[g].y);
 }
 void cast_d2f(const double2* X, float2* Y, int64_t count, cudaStream_t st) {
-  if (count) k_d2f<<<grid_for(count, 256), 256, 0, st>>>(X, Y, count);
+  if (count) { k_d2f<<<grid_for(count, 256), 256, 0, st>>>(X, Y, count); count_launch(); }
 }
 void cast_f2d(const float2* X, double2* Y, int64_t count, cudaStream_t st) {
-  if (count) k_f2d<<<grid_for(count, 256), 256, 0, st>>>(X, Y, count);
+  if (count) { k_f2d<<<grid_for(count, 256), 256, 0, st>>>(X, Y, count); count_launch(); }
 }
 
 }  // namespace hz

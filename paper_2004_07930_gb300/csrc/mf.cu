@@ -15,9 +15,13 @@
 //   forward  (leaves to root): t = X_t b_P;  y_P = t[0:k] / D;
 //                              parent update  w = c_U + t[k:f]
 //   backward (root to leaves): x_P = X_t^T [y_P; x_U]
-// so that both sweeps are streaming matrix products (forward: one thread per
-// factor row; backward: one warp per pivot column) spread over all SMs, in
-// FP64 or (mixed form) in FP32.
+// so that each level of each sweep is two flat launches: fixed-size
+// 128 x 256 factor tiles split along the reduction (balanced over all SMs
+// whatever the front sizes; the extend-add of the children's update vectors
+// is done while staging the input), and a fixed-order sum of the tiles'
+// partial results. FP64, or FP32 in the mixed
+// form. X_t is stored twice, column-major and transposed, so that both
+// sweeps read their factor with unit stride across a warp.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -153,7 +157,7 @@ template <typename V>
 __global__ void k_mf_inverse(const int* __restrict__ list, const int* __restrict__ kk, const int* __restrict__ ff,
                              const int64_t* __restrict__ Foff, const int64_t* __restrict__ Moff,
                              const int64_t* __restrict__ Doff, double2* __restrict__ F, V* __restrict__ M,
-                             V* __restrict__ Dinv) {
+                             V* __restrict__ MT, V* __restrict__ Dinv) {
   extern __shared__ double2 col[];
   const int t = list[blockIdx.x];
   const int f = ff[t], k = kk[t];
@@ -182,15 +186,24 @@ __global__ void k_mf_inverse(const int* __restrict__ list, const int* __restrict
     __syncthreads();
   }
   V* Mt = M + Moff[t];
+  V* MTt = MT + Moff[t];
   const int64_t fk = (int64_t)f * k;
   for (int64_t i = threadIdx.x; i < fk; i += blockDim.x) {
     int r = (int)(i % f), c = (int)(i / f);
     double2 v = r == c ? make_double2(1.0, 0.0) : (r < c ? make_double2(0.0, 0.0) : Ft[i]);
     Mt[i] = from_d<V>(v);
+    MTt[c + (int64_t)r * k] = from_d<V>(v);
   }
 }
 
+template <typename V>
+static void tile_attrs_all();
+
 void mf_factor(DevMF& mf, double tau_abs, cudaStream_t st) {
+  if (mf.fp32)
+    tile_attrs_all<float2>();
+  else
+    tile_attrs_all<double2>();
   size_t shm = (size_t)std::max(mf.max_f, 1) * sizeof(double2);
   cudaFuncSetAttribute(k_mf_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   cudaFuncSetAttribute(k_mf_inverse<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
@@ -198,9 +211,9 @@ void mf_factor(DevMF& mf, double tau_abs, cudaStream_t st) {
   for (int l = 0; l < mf.nlevels; ++l) {
     int b = mf.level_ptr_h[l], e = mf.level_ptr_h[l + 1];
     if (e == b) continue;
-    k_mf_assemble<<<e - b, 256, 0, st>>>(mf.level_list + b, mf.k, mf.f, mf.Foff, mf.rowoff, mf.cmap, mf.child_ptr,
-                                         mf.child_idx, mf.amap_ptr, mf.amap_pos, mf.amap_val, mf.Aval, mf.F);
-    k_mf_factor<<<e - b, 256, shm, st>>>(mf.level_list + b, mf.k, mf.f, mf.Foff, mf.F, tau_abs, mf.perturbed);
+    { k_mf_assemble<<<e - b, 256, 0, st>>>(mf.level_list + b, mf.k, mf.f, mf.Foff, mf.rowoff, mf.cmap, mf.child_ptr,
+                                         mf.child_idx, mf.amap_ptr, mf.amap_pos, mf.amap_val, mf.Aval, mf.F); count_launch(); }
+    { k_mf_factor<<<e - b, 256, shm, st>>>(mf.level_list + b, mf.k, mf.f, mf.Foff, mf.F, tau_abs, mf.perturbed); count_launch(); }
   }
   // the inverses only touch the pivot columns: run them after every Schur
   // complement has been consumed by its parent
@@ -208,223 +221,290 @@ void mf_factor(DevMF& mf, double tau_abs, cudaStream_t st) {
     int b = mf.level_ptr_h[l], e = mf.level_ptr_h[l + 1];
     if (e == b) continue;
     if (mf.fp32)
-      k_mf_inverse<float2><<<e - b, 256, shm, st>>>(mf.level_list + b, mf.k, mf.f, mf.Foff, mf.Moff, mf.Doff, mf.F,
-                                                    (float2*)mf.M, (float2*)mf.Dinv);
+      { k_mf_inverse<float2><<<e - b, 256, shm, st>>>(mf.level_list + b, mf.k, mf.f, mf.Foff, mf.Moff, mf.Doff, mf.F,
+                                                    (float2*)mf.M, (float2*)mf.MT, (float2*)mf.Dinv); count_launch(); }
     else
-      k_mf_inverse<double2><<<e - b, 256, shm, st>>>(mf.level_list + b, mf.k, mf.f, mf.Foff, mf.Moff, mf.Doff,
-                                                     mf.F, (double2*)mf.M, (double2*)mf.Dinv);
+      { k_mf_inverse<double2><<<e - b, 256, shm, st>>>(mf.level_list + b, mf.k, mf.f, mf.Foff, mf.Moff, mf.Doff,
+                                                     mf.F, (double2*)mf.M, (double2*)mf.MT, (double2*)mf.Dinv); count_launch(); }
   }
 }
 
 // ---------------------------------------------------------------------------
 // Solve sweeps
 // ---------------------------------------------------------------------------
-constexpr int FWD_ROWS = 128;  // rows per forward tile: one thread per row
-constexpr int BWD_COLS = 8;    // pivots per backward tile: one warp per pivot
+constexpr int MF_TILE = 128;  // output rows per tile (MF_TILE_ROWS on the host)
+constexpr int MF_TK = 128;    // reduction length per tile (MF_TILE_K on the host)
 
-// front vector: Win[0:k] = Xsub[pivots], Win[k:f] = 0, plus the children's
-// update vectors (Wout[k_c:f_c] of each child) added at their parent rows
-template <typename V>
-__global__ void k_mf_fvec(const int* __restrict__ list, const int* __restrict__ kk, const int* __restrict__ ff,
-                          const int64_t* __restrict__ rowoff, const int* __restrict__ rows,
-                          const int* __restrict__ cmap, const int* __restrict__ child_ptr,
-                          const int* __restrict__ child_idx, const V* __restrict__ Xsub, V* __restrict__ Win,
-                          const V* __restrict__ Wout, int s) {
-  const int t = list[blockIdx.x];
+// Input value of front row R (column c) of a sweep:
+//   forward : b_P at a pivot row = the sub-vector entry plus the children's
+//             update vectors that land on it (extend-add, child order)
+//   backward: y_P (kept in Wout by the forward sweep) at a pivot row, the
+//             final value of the ancestor's pivot (sub-vector) at an update row
+template <typename V, bool FWD>
+__device__ __forceinline__ V sweep_input(int64_t R, int local, int k, int c, int s, const int* __restrict__ rows,
+                                         const int64_t* __restrict__ cptr, const int* __restrict__ cidx,
+                                         const V* __restrict__ Xsub, const V* __restrict__ Wout) {
+  if (FWD) {
+    V v = Xsub[(int64_t)rows[R] * s + c];
+    for (int64_t p = cptr[R]; p < cptr[R + 1]; ++p) v = c_add(v, Wout[(int64_t)cidx[p] * s + c]);
+    return v;
+  }
+  return local < k ? Wout[R * s + c] : Xsub[(int64_t)rows[R] * s + c];
+}
+
+// One tile: MF_TILE output rows x MF_TK reduction indices of
+//   forward : t = X_t b_P      (X_t column-major f x k)
+//   backward: x = X_t^T v      (X_t^T column-major k x f, v = [y_P; x_U])
+// A row block covered by one tile (slot < 0) applies the epilogue directly;
+// otherwise the tile writes a partial result to its slot of P and the row
+// block's partials are summed in a fixed order by k_mf_reduce. Epilogue:
+//   forward : rows r < k -> y = t / D (kept in Wout for the backward sweep);
+//             rows r >= k -> parent update c_U + t (Wout), c_U = the children's
+//             update vectors landing on the row
+//   backward: x at the pivot rows of the sub-vector
+// Each thread owns R output rows
+// (NT apart, so a warp reads 32 consecutive factor entries per column) and
+// the s right-hand sides as register accumulators; chunks of the input vector
+// are staged in shared memory and read as broadcasts.
+template <typename V, int S, int R, int NT, int G, bool FWD>
+__global__ void __launch_bounds__(NT * G) k_mf_tile(const int4* __restrict__ tiles, const int* __restrict__ kk,
+                                                    const int* __restrict__ ff, const int64_t* __restrict__ rowoff,
+                                                    const int64_t* __restrict__ Moff, const V* __restrict__ M,
+                                                    const int* __restrict__ rows, const int64_t* __restrict__ cptr,
+                                                    const int* __restrict__ cidx, const int64_t* __restrict__ Doff,
+                                                    const V* __restrict__ Dinv, V* __restrict__ Xsub,
+                                                    V* __restrict__ Wout, V* __restrict__ P, int s) {
+  static_assert(NT * R == MF_TILE, "tile height");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V(*bs)[S] = reinterpret_cast<V(*)[S]>(smem_raw);                            // [MF_TK][S] tile input
+  V(*red)[S] = reinterpret_cast<V(*)[S]>(smem_raw + sizeof(V) * MF_TK * S);  // [(G-1) MF_TILE][S]
+  const int4 tile = tiles[blockIdx.x];
+  const int t = tile.x, r0 = tile.y, c0 = tile.z, slot = tile.w;
   const int f = ff[t], k = kk[t];
-  const int* rt = rows + rowoff[t];
-  V* fv = Win + rowoff[t] * s;
-  for (int i = threadIdx.x; i < f * s; i += blockDim.x) {
-    int r = i / s, c = i - r * s;
-    fv[i] = r < k ? Xsub[(int64_t)rt[r] * s + c] : mk2((decltype(V::x))0, (decltype(V::x))0);
+  const int nout = FWD ? f : k;
+  const int ld = FWD ? f : k;
+  const int kend = FWD ? ((r0 < k) ? min(k, r0 + MF_TILE) : k) : f;
+  const int kbeg = FWD ? c0 : max(c0, r0);  // X_t^T is zero left of the diagonal of its pivot block
+  const int kstop = min(kend, c0 + MF_TK);
+  const V* Mt = M + Moff[t];
+  const int64_t ro = rowoff[t];
+  const int grp = threadIdx.x / NT, tid = threadIdx.x % NT;
+  const int lmax = max(0, kstop - kbeg);
+  const int per = (lmax + G - 1) / G;
+  const int l0 = min(lmax, grp * per), l1 = min(lmax, l0 + per);
+  const V* mrow[R];
+  bool act[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int rr = r0 + tid + q * NT;
+    act[q] = rr < nout;
+    mrow[q] = Mt + (act[q] ? rr : 0) + (int64_t)kbeg * ld;
+  }
+  // first factor entries in flight while the inputs are staged
+  constexpr int PF = 8;
+  V pre[PF][R];
+#pragma unroll
+  for (int u = 0; u < PF; ++u)
+#pragma unroll
+    for (int q = 0; q < R; ++q)
+      pre[u][q] = (act[q] && l0 + u < l1) ? mrow[q][(int64_t)(l0 + u) * ld] : mk2((decltype(V::x))0, (decltype(V::x))0);
+  for (int i = threadIdx.x; i < lmax * S; i += NT * G) {
+    const int l = i / S, c = i % S;
+    V v = mk2((decltype(V::x))0, (decltype(V::x))0);
+    if (c < s) v = sweep_input<V, FWD>(ro + kbeg + l, kbeg + l, k, c, s, rows, cptr, cidx, Xsub, Wout);
+    bs[l][c] = v;
   }
   __syncthreads();
-  for (int q = child_ptr[t]; q < child_ptr[t + 1]; ++q) {
-    const int ch = child_idx[q];
-    const int kc = kk[ch], mc = ff[ch] - kc;
-    const V* wc = Wout + (rowoff[ch] + kc) * s;
-    const int* cm = cmap + rowoff[ch] + kc;
-    for (int i = threadIdx.x; i < mc * s; i += blockDim.x) {
-      int a = i / s, c = i - a * s;
-      fv[cm[a] * s + c] = c_add(fv[cm[a] * s + c], wc[i]);
+  V acc[R][S];
+#pragma unroll
+  for (int q = 0; q < R; ++q)
+#pragma unroll
+    for (int c = 0; c < S; ++c) acc[q][c] = mk2((decltype(V::x))0, (decltype(V::x))0);
+  {
+    // the G thread groups split the tile's reduction range
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      if (l0 + u >= l1) break;
+#pragma unroll
+      for (int c = 0; c < S; ++c) {
+        const V b = bs[l0 + u][c];
+#pragma unroll
+        for (int q = 0; q < R; ++q) acc[q][c] = c_fma(pre[u][q], b, acc[q][c]);
+      }
+    }
+#pragma unroll 8
+    for (int l = l0 + PF; l < l1; ++l) {
+      V m[R];
+#pragma unroll
+      for (int q = 0; q < R; ++q)
+        m[q] = act[q] ? mrow[q][(int64_t)l * ld] : mk2((decltype(V::x))0, (decltype(V::x))0);
+#pragma unroll
+      for (int c = 0; c < S; ++c) {
+        const V b = bs[l][c];
+#pragma unroll
+        for (int q = 0; q < R; ++q) acc[q][c] = c_fma(m[q], b, acc[q][c]);
+      }
+    }
+  }
+  if (G > 1) {
+    if (grp > 0) {
+#pragma unroll
+      for (int q = 0; q < R; ++q)
+#pragma unroll
+        for (int c = 0; c < S; ++c) red[(grp - 1) * MF_TILE + tid + q * NT][c] = acc[q][c];
     }
     __syncthreads();
+    if (grp > 0) return;
+#pragma unroll
+    for (int g = 1; g < G; ++g)
+#pragma unroll
+      for (int q = 0; q < R; ++q)
+#pragma unroll
+        for (int c = 0; c < S; ++c) acc[q][c] = c_add(acc[q][c], red[(g - 1) * MF_TILE + tid + q * NT][c]);
+  }
+  if (slot >= 0) {
+    V* out = P + (int64_t)slot * MF_TILE * s;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int i = tid + q * NT;
+#pragma unroll
+      for (int c = 0; c < S; ++c)
+        if (c < s) out[i * s + c] = acc[q][c];
+    }
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int rr = r0 + tid + q * NT;
+    if (rr >= nout) continue;
+    const int64_t Rg = ro + rr;
+    if (FWD) {
+      if (rr < k) {
+        const V di = Dinv[Doff[t] + rr];
+#pragma unroll
+        for (int c = 0; c < S; ++c)
+          if (c < s) Wout[Rg * s + c] = c_mul(acc[q][c], di);
+      } else {
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+          if (c >= s) continue;
+          V a = acc[q][c];
+          for (int64_t p = cptr[Rg]; p < cptr[Rg + 1]; ++p) a = c_add(a, Wout[(int64_t)cidx[p] * s + c]);
+          Wout[Rg * s + c] = a;
+        }
+      }
+    } else {
+      V* xo = Xsub + (int64_t)rows[Rg] * s;
+#pragma unroll
+      for (int c = 0; c < S; ++c)
+        if (c < s) xo[c] = acc[q][c];
+    }
   }
 }
 
-// Forward tile: rows [r0, r0 + FWD_ROWS) of t = X_t b_P. One thread per row
-// streams its row of X_t (consecutive threads read consecutive addresses of
-// the column-major factor) against chunks of b_P staged in shared memory;
-// the s right-hand sides are register accumulators, so every factor entry
-// is read from HBM once per sweep.
-template <typename V, int S>
-__global__ void __launch_bounds__(FWD_ROWS) k_mf_fwd(const int2* __restrict__ tiles, const int* __restrict__ kk,
-                                                     const int* __restrict__ ff, const int64_t* __restrict__ rowoff,
-                                                     const int64_t* __restrict__ Moff, const int64_t* __restrict__ Doff,
-                                                     const V* __restrict__ M, const V* __restrict__ Dinv,
-                                                     const V* __restrict__ Win, V* __restrict__ Wout, int s) {
-  constexpr int KC = (S >= 32) ? 32 : 64;
-  __shared__ V bs[KC][S];
-  const int2 tile = tiles[blockIdx.x];
-  const int t = tile.x, r0 = tile.y;
-  const int f = ff[t], k = kk[t];
-  const int r = r0 + threadIdx.x;
-  const bool active = r < f;
-  const V* Mr = M + Moff[t] + r;
-  const int64_t ro = rowoff[t];
-  const V* bin = Win + ro * s;
-  const int kend = (r0 < k) ? min(k, r0 + FWD_ROWS) : k;
-  V acc[S];
-#pragma unroll
-  for (int c = 0; c < S; ++c) acc[c] = mk2((decltype(V::x))0, (decltype(V::x))0);
-  for (int k0 = 0; k0 < kend; k0 += KC) {
-    const int lmax = min(KC, kend - k0);
-    for (int i = threadIdx.x; i < KC * S; i += FWD_ROWS) {
-      int l = i / S, c = i % S;
-      bs[l][c] = (l < lmax && c < s) ? bin[(k0 + l) * s + c] : mk2((decltype(V::x))0, (decltype(V::x))0);
+// Row-block epilogue, one thread per (row, column): sum the row block's
+// partial tiles in order, then
+//   forward : rows r < k -> y = t / D (kept in Wout for the backward sweep);
+//             rows r >= k -> parent update c_U + t (Wout), c_U = the children's
+//             update vectors landing on the row
+//   backward: x at the pivot rows of the sub-vector
+template <typename V, bool FWD>
+__global__ void k_mf_reduce(const int4* __restrict__ rblocks, int nrb, const int* __restrict__ kk,
+                            const int* __restrict__ ff, const int64_t* __restrict__ rowoff,
+                            const int64_t* __restrict__ Doff, const int* __restrict__ rows,
+                            const int64_t* __restrict__ cptr, const int* __restrict__ cidx,
+                            const V* __restrict__ Dinv, V* __restrict__ Wout, const V* __restrict__ P,
+                            V* __restrict__ Xsub, int s) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)MF_TILE * s;
+  if (g >= nrb * per) return;
+  const int4 rb = rblocks[g / per];
+  const int i = (int)((g % per) / s), c = (int)(g % s);
+  const int t = rb.x, r = rb.y + i;
+  const int k = kk[t];
+  if (r >= (FWD ? ff[t] : k)) return;
+  V acc = mk2((decltype(V::x))0, (decltype(V::x))0);
+  for (int q = 0; q < rb.z; ++q) acc = c_add(acc, P[((int64_t)(rb.w + q) * MF_TILE + i) * s + c]);
+  const int64_t R = rowoff[t] + r;
+  if (FWD) {
+    if (r < k) {
+      Wout[R * s + c] = c_mul(acc, Dinv[Doff[t] + r]);
+    } else {
+      for (int64_t p = cptr[R]; p < cptr[R + 1]; ++p) acc = c_add(acc, Wout[(int64_t)cidx[p] * s + c]);
+      Wout[R * s + c] = acc;
     }
-    __syncthreads();
-    if (active) {
-#pragma unroll 4
-      for (int l = 0; l < lmax; ++l) {
-        const V m = Mr[(int64_t)(k0 + l) * f];
-#pragma unroll
-        for (int c = 0; c < S; ++c) acc[c] = c_fma(m, bs[l][c], acc[c]);
-      }
-    }
-    __syncthreads();
-  }
-  if (!active) return;
-  V* out = Wout + (ro + r) * s;
-  if (r < k) {
-    const V di = Dinv[Doff[t] + r];
-#pragma unroll
-    for (int c = 0; c < S; ++c)
-      if (c < s) out[c] = c_mul(acc[c], di);
   } else {
-    const V* in = bin + (int64_t)r * s;
-#pragma unroll
-    for (int c = 0; c < S; ++c)
-      if (c < s) out[c] = c_add(in[c], acc[c]);
+    Xsub[(int64_t)rows[R] * s + c] = acc;
   }
 }
 
-// backward: Win[k:f] = x_U gathered from the (final) ancestor pivots
-template <typename V>
-__global__ void k_mf_bvec(const int* __restrict__ list, const int* __restrict__ kk, const int* __restrict__ ff,
-                          const int64_t* __restrict__ rowoff, const int* __restrict__ rows,
-                          const V* __restrict__ Xsub, V* __restrict__ Win, int s) {
-  const int t = list[blockIdx.x];
-  const int f = ff[t], k = kk[t];
-  const int* rt = rows + rowoff[t];
-  V* fv = Win + rowoff[t] * s;
-  for (int i = k * s + threadIdx.x; i < f * s; i += blockDim.x) {
-    int r = i / s, c = i - r * s;
-    fv[i] = Xsub[(int64_t)rt[r] * s + c];
-  }
+static inline unsigned blocks_for(int64_t work, int b) { return (unsigned)((work + b - 1) / b); }
+
+template <typename V, int S, int R, int NT, int G>
+static constexpr size_t tile_smem() {
+  return sizeof(V) * (size_t)S * (MF_TK + (G - 1) * MF_TILE);
 }
 
-// Backward tile: pivots [j0, j0 + BWD_COLS) of x_P = X_t^T [y_P; x_U]. One
-// warp per pivot column j: the lanes stream column j of X_t (contiguous)
-// against chunks of the front vector staged in shared memory, then reduce.
-template <typename V, int S>
-__global__ void __launch_bounds__(32 * BWD_COLS) k_mf_bwd(const int2* __restrict__ tiles, const int* __restrict__ kk,
-                                                          const int* __restrict__ ff,
-                                                          const int64_t* __restrict__ rowoff,
-                                                          const int64_t* __restrict__ Moff, const int* __restrict__ rows,
-                                                          const V* __restrict__ M, const V* __restrict__ Win,
-                                                          const V* __restrict__ Wout, V* __restrict__ Xsub, int s) {
-  constexpr int RC = (S >= 32) ? 32 : 64;
-  __shared__ V vs[RC][S + 1];
-  const int2 tile = tiles[blockIdx.x];
-  const int t = tile.x, j0 = tile.y;
-  const int f = ff[t], k = kk[t];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int j = j0 + w;
-  const int64_t ro = rowoff[t];
-  const V* Mj = M + Moff[t] + (int64_t)j * f;
-  V acc[S];
-#pragma unroll
-  for (int c = 0; c < S; ++c) acc[c] = mk2((decltype(V::x))0, (decltype(V::x))0);
-  for (int r0 = j0; r0 < f; r0 += RC) {
-    const int lmax = min(RC, f - r0);
-    for (int i = threadIdx.x; i < RC * S; i += 32 * BWD_COLS) {
-      int l = i / S, c = i % S;
-      V v = mk2((decltype(V::x))0, (decltype(V::x))0);
-      if (l < lmax && c < s) {
-        const int gr = r0 + l;
-        v = gr < k ? Wout[(ro + gr) * s + c] : Win[(ro + gr) * s + c];
-      }
-      vs[l][c] = v;
-    }
-    __syncthreads();
-    if (j < k) {
-      for (int l = lane; l < lmax; l += 32) {
-        const int gr = r0 + l;
-        if (gr < j) continue;  // X_t is zero above the diagonal of its pivot block
-        const V m = Mj[gr];
-#pragma unroll
-        for (int c = 0; c < S; ++c) acc[c] = c_fma(m, vs[l][c], acc[c]);
-      }
-    }
-    __syncthreads();
-  }
-  if (j >= k) return;
-#pragma unroll
-  for (int c = 0; c < S; ++c)
-    for (int o = 16; o > 0; o >>= 1) {
-      acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, o);
-      acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, o);
-    }
-  V* xo = Xsub + (int64_t)rows[ro + j] * s;
-#pragma unroll
-  for (int c = 0; c < S; ++c)
-    if (c < s && c % 32 == lane) xo[c] = acc[c];
-}
-
-template <typename V, int S>
+template <typename V, int S, int R, int NT, int G>
 static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
-  V* Win = (V*)mf.Win;
+  const size_t shm = tile_smem<V, S, R, NT, G>();
   V* Wout = (V*)mf.Wout;
+  V* P = (V*)mf.P;
   const V* M = (const V*)mf.M;
+  const V* MT = (const V*)mf.MT;
   const V* Dv = (const V*)mf.Dinv;
   for (int l = 0; l < mf.nlevels; ++l) {
-    int b = mf.level_ptr_h[l], e = mf.level_ptr_h[l + 1];
-    if (e == b) continue;
-    k_mf_fvec<V><<<e - b, 256, 0, st>>>(mf.level_list + b, mf.k, mf.f, mf.rowoff, mf.rows, mf.cmap, mf.child_ptr,
-                                        mf.child_idx, Xsub, Win, Wout, s);
-    int tb = mf.ftile_ptr_h[l], te = mf.ftile_ptr_h[l + 1];
+    const int tb = mf.ftile_ptr_h[l], te = mf.ftile_ptr_h[l + 1];
     if (te > tb)
-      k_mf_fwd<V, S><<<te - tb, FWD_ROWS, 0, st>>>(mf.ftiles + tb, mf.k, mf.f, mf.rowoff, mf.Moff, mf.Doff, M, Dv,
-                                                   Win, Wout, s);
+      { k_mf_tile<V, S, R, NT, G, true><<<te - tb, NT * G, shm, st>>>(mf.ftiles + tb, mf.k, mf.f, mf.rowoff, mf.Moff, M, mf.rows,
+                                                           mf.cptr, mf.cidx, mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
+    const int rb = mf.frb_ptr_h[l], re = mf.frb_ptr_h[l + 1];
+    if (re > rb)
+      { k_mf_reduce<V, true><<<blocks_for((int64_t)(re - rb) * MF_TILE * s, 256), 256, 0, st>>>(
+          mf.frb + rb, re - rb, mf.k, mf.f, mf.rowoff, mf.Doff, mf.rows, mf.cptr, mf.cidx, Dv, Wout, P, Xsub, s); count_launch(); }
   }
   for (int l = mf.nlevels - 1; l >= 0; --l) {
-    int b = mf.level_ptr_h[l], e = mf.level_ptr_h[l + 1];
-    if (e == b) continue;
-    k_mf_bvec<V><<<e - b, 256, 0, st>>>(mf.level_list + b, mf.k, mf.f, mf.rowoff, mf.rows, Xsub, Win, s);
-    int tb = mf.btile_ptr_h[l], te = mf.btile_ptr_h[l + 1];
+    const int tb = mf.btile_ptr_h[l], te = mf.btile_ptr_h[l + 1];
     if (te > tb)
-      k_mf_bwd<V, S><<<te - tb, 32 * BWD_COLS, 0, st>>>(mf.btiles + tb, mf.k, mf.f, mf.rowoff, mf.Moff, mf.rows, M,
-                                                        Win, Wout, Xsub, s);
+      { k_mf_tile<V, S, R, NT, G, false><<<te - tb, NT * G, shm, st>>>(mf.btiles + tb, mf.k, mf.f, mf.rowoff, mf.Moff, MT,
+                                                            mf.rows, mf.cptr, mf.cidx, mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
+    const int rb = mf.brb_ptr_h[l], re = mf.brb_ptr_h[l + 1];
+    if (re > rb)
+      { k_mf_reduce<V, false><<<blocks_for((int64_t)(re - rb) * MF_TILE * s, 256), 256, 0, st>>>(
+          mf.brb + rb, re - rb, mf.k, mf.f, mf.rowoff, mf.Doff, mf.rows, mf.cptr, mf.cidx, Dv, Wout, P, Xsub, s); count_launch(); }
   }
+}
+
+// Opt the tile kernels into their dynamic shared memory once, outside any
+// stream capture (called from the factorisation).
+template <typename V, int S, int R, int NT, int G>
+static void tile_attrs() {
+  const int shm = (int)tile_smem<V, S, R, NT, G>();
+  cudaFuncSetAttribute(k_mf_tile<V, S, R, NT, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+  cudaFuncSetAttribute(k_mf_tile<V, S, R, NT, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+}
+
+// (S, R, NT, G): right-hand sides in registers, rows per thread, threads per
+// group (NT * R = 128 rows), groups splitting the reduction range
+#define HZ_TILE_CONFIGS(X) \
+  X(1, 1, 128, 1) X(2, 1, 128, 1) X(4, 1, 128, 1) X(8, 1, 128, 1) X(16, 1, 128, 1) X(32, 1, 128, 1) X(64, 1, 128, 1)
+
+template <typename V>
+static void tile_attrs_all() {
+#define HZ_ATTR(S, R, NT, G) tile_attrs<V, S, R, NT, G>();
+  HZ_TILE_CONFIGS(HZ_ATTR)
+#undef HZ_ATTR
 }
 
 template <typename V>
 static void solve_dispatch(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
-  if (s <= 1)
-    solve_impl<V, 1>(mf, Xsub, s, st);
-  else if (s <= 2)
-    solve_impl<V, 2>(mf, Xsub, s, st);
-  else if (s <= 4)
-    solve_impl<V, 4>(mf, Xsub, s, st);
-  else if (s <= 8)
-    solve_impl<V, 8>(mf, Xsub, s, st);
-  else if (s <= 16)
-    solve_impl<V, 16>(mf, Xsub, s, st);
-  else if (s <= 32)
-    solve_impl<V, 32>(mf, Xsub, s, st);
-  else
-    solve_impl<V, 64>(mf, Xsub, s, st);
+#define HZ_CASE(S, R, NT, G)                         \
+  if (s <= S) {                                      \
+    solve_impl<V, S, R, NT, G>(mf, Xsub, s, st);     \
+    return;                                          \
+  }
+  HZ_TILE_CONFIGS(HZ_CASE)
+#undef HZ_CASE
 }
 
 void mf_solve(DevMF& mf, void* Xsub, int s, cudaStream_t st) {
@@ -465,13 +545,13 @@ __global__ void k_scatter_owned_f32(const int* __restrict__ own, int64_t n, cons
 
 void gather_rows_f32(const int* idx, int64_t nrows, const double2* X, float2* Y, int s, cudaStream_t st) {
   if (nrows * s == 0) return;
-  k_gather_rows_f32<<<(unsigned)((nrows * s + 255) / 256), 256, 0, st>>>(idx, nrows, X, Y, s);
+  { k_gather_rows_f32<<<(unsigned)((nrows * s + 255) / 256), 256, 0, st>>>(idx, nrows, X, Y, s); count_launch(); }
 }
 
 void scatter_owned_f32(const int* own, int64_t n, const float2* Xsub, const double2* Q, double2* Z, int s,
                        cudaStream_t st) {
   if (n * s == 0) return;
-  k_scatter_owned_f32<<<(unsigned)((n * s + 255) / 256), 256, 0, st>>>(own, n, Xsub, Q, Z, s);
+  { k_scatter_owned_f32<<<(unsigned)((n * s + 255) / 256), 256, 0, st>>>(own, n, Xsub, Q, Z, s); count_launch(); }
 }
 
 }  // namespace hz

@@ -48,7 +48,8 @@ class HzInfo(C.Structure):
                 ("sub_rows", C.c_int64), ("n_coarse", C.c_int64), ("nnz_coarse", C.c_int64),
                 ("factor_entries", C.c_int64), ("coarse_factor_entries", C.c_int64),
                 ("front_entries", C.c_int64), ("max_front", C.c_int32), ("nfronts", C.c_int32),
-                ("nlevels", C.c_int32), ("perturbed_pivots", C.c_int32), ("device_bytes", C.c_double)]
+                ("nlevels", C.c_int32), ("perturbed_pivots", C.c_int32), ("device_bytes", C.c_double),
+                ("kernel_launches", C.c_int64)]
 
     def asdict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
