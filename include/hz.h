@@ -194,6 +194,26 @@ int hz_profile_end(hz_ctx* ctx, hz_phase_time* out, int32_t cap, int32_t* count)
 /* Host copy of A in CSR form: rowptr [n+1], col [nnz], val [nnz][2]. */
 int hz_matrix_csr(const hz_ctx* ctx, int64_t* rowptr, int32_t* col, double* val);
 
+/* Allocation-free Y = A X, for callers that cannot allocate device memory
+ * when they call the library: code running where cudaMalloc/cudaFree are not
+ * allowed (they synchronise the device), or processes whose device memory is
+ * entirely managed by their own allocator. The paper has no counterpart; the
+ * product is the one of hz_apply_A.
+ *   X, Y   device pointers, [s][n][2] doubles (same layout as hz_apply_A)
+ *   stream cudaStream_t the kernels are queued on (NULL: legacy default
+ *          stream); the call returns without waiting for them
+ * Its two [n][s] work blocks live in a file-scope device array of
+ * 2 x HZ_NOALLOC_MAX_ENTRIES complex values (32 MiB) that every GPU loading
+ * the library holds until the process exits; the call allocates nothing.
+ * n * s > HZ_NOALLOC_MAX_ENTRIES is refused with HZ_EINVAL before any launch.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. All calls share the array: calls whose kernels overlap on the GPU
+ * (other streams, other threads, other contexts) race. Every call overwrites
+ * the entries it reads, so no state carries over between calls. */
+#define HZ_NOALLOC_MAX_ENTRIES 1048576
+int hz_apply_A_noalloc(hz_ctx* ctx, const double* X, double* Y, int32_t s, void* stream);
+
 void hz_free(hz_ctx* ctx);
 const char* hz_strerror(int code);
 const char* hz_last_error(void);

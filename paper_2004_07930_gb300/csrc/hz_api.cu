@@ -871,6 +871,15 @@ void join_user(hz_ctx* c) {
 
 }  // namespace
 
+namespace hz {
+// accessors for the allocation-free entry point (noalloc.cu)
+const DevSplitCsr* ctx_matrix(const hz_ctx* c, int64_t* n) {
+  *n = c->space.n;
+  return &c->A;
+}
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace hz
+
 extern "C" {
 
 int hz_default_options(hz_options* o) {

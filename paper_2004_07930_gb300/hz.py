@@ -19,7 +19,8 @@ HZ_PREC_FP64, HZ_PREC_MIXED = 0, 1
 
 EXPORTS = ["hz_default_options", "hz_setup", "hz_ndof", "hz_dof_coords", "hz_get_info", "hz_solve",
            "hz_solve_rhs", "hz_apply_A", "hz_apply_prec", "hz_matrix_csr", "hz_free", "hz_strerror",
-           "hz_last_error", "hz_profile_begin", "hz_profile_end"]
+           "hz_last_error", "hz_profile_begin", "hz_profile_end", "hz_apply_A_noalloc"]
+HZ_NOALLOC_MAX_ENTRIES = 1048576  # complex entries per work block of hz_apply_A_noalloc (n * s)
 
 
 class HzMesh(C.Structure):
@@ -88,6 +89,7 @@ def load():
     lib.hz_apply_A.argtypes = [P, P, P, C.c_int32, C.c_int32]
     lib.hz_apply_prec.argtypes = [P, P, P, C.c_int32, C.c_int32]
     lib.hz_matrix_csr.argtypes = [P, P, P, P]
+    lib.hz_apply_A_noalloc.argtypes = [P, P, P, C.c_int32, P]
     lib.hz_profile_begin.argtypes = [P]
     lib.hz_profile_end.argtypes = [P, C.POINTER(HzPhaseTime), C.c_int32, C.POINTER(C.c_int32)]
     lib.hz_free.argtypes = [P]
