@@ -56,12 +56,14 @@ __global__ void k_spmm_split(int64_t n, int s, const int64_t* __restrict__ rp_re
   int c = (int)(g - r * s);
   if (r >= n) return;
   double ar = 0.0, ai = 0.0;
+  #pragma unroll 4
   for (int64_t p = rp_re[r], pe = rp_re[r + 1]; p < pe; ++p) {
     double a = val_re[p];
     double2 x = X[(int64_t)col_re[p] * s + c];
     ar = fma(a, x.x, ar);
     ai = fma(a, x.y, ai);
   }
+  #pragma unroll 4
   for (int64_t p = rp_im[r], pe = rp_im[r + 1]; p < pe; ++p) {
     double b = val_im[p];
     double2 x = X[(int64_t)col_im[p] * s + c];
@@ -91,6 +93,7 @@ __global__ void k_spmm_real(int64_t n, int s, const int64_t* __restrict__ rp, co
   int c = (int)(g - r * s);
   if (r >= n) return;
   double ar = 0.0, ai = 0.0;
+  #pragma unroll 4
   for (int64_t p = rp[r], pe = rp[r + 1]; p < pe; ++p) {
     double a = val[p];
     double2 x = X[(int64_t)col[p] * s + c];

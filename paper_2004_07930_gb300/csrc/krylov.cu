@@ -339,12 +339,14 @@ __global__ void k_spmm_split_f32(int64_t n, int s, const int64_t* __restrict__ r
   int c = (int)(g - r * s);
   if (r >= n) return;
   float ar = 0.f, ai = 0.f;
+  #pragma unroll 4
   for (int64_t p = rp_re[r], pe = rp_re[r + 1]; p < pe; ++p) {
     float a = val_re[p];
     float2 x = X[(int64_t)col_re[p] * s + c];
     ar = fmaf(a, x.x, ar);
     ai = fmaf(a, x.y, ai);
   }
+  #pragma unroll 4
   for (int64_t p = rp_im[r], pe = rp_im[r + 1]; p < pe; ++p) {
     float b = val_im[p];
     float2 x = X[(int64_t)col_im[p] * s + c];
@@ -373,6 +375,7 @@ __global__ void k_spmm_real_f32(int64_t n, int s, const int64_t* __restrict__ rp
   int c = (int)(g - r * s);
   if (r >= n) return;
   float ar = 0.f, ai = 0.f;
+  #pragma unroll 4
   for (int64_t p = rp[r], pe = rp[r + 1]; p < pe; ++p) {
     float a = val[p];
     float2 x = X[(int64_t)col[p] * s + c];

@@ -235,26 +235,13 @@ void mf_factor(DevMF& mf, double tau_abs, cudaStream_t st) {
 constexpr int MF_TILE = 128;  // output rows per tile (MF_TILE_ROWS on the host)
 constexpr int MF_TK = 128;    // reduction length per tile (MF_TILE_K on the host)
 
-// Input value of front row R (column c) of a sweep:
-//   forward : b_P at a pivot row = the sub-vector entry plus the children's
-//             update vectors that land on it (extend-add, child order)
-//   backward: y_P (kept in Wout by the forward sweep) at a pivot row, the
-//             final value of the ancestor's pivot (sub-vector) at an update row
-template <typename V, bool FWD>
-__device__ __forceinline__ V sweep_input(int64_t R, int local, int k, int c, int s, const int* __restrict__ rows,
-                                         const int64_t* __restrict__ cptr, const int* __restrict__ cidx,
-                                         const V* __restrict__ Xsub, const V* __restrict__ Wout) {
-  if (FWD) {
-    V v = Xsub[(int64_t)rows[R] * s + c];
-    for (int64_t p = cptr[R]; p < cptr[R + 1]; ++p) v = c_add(v, Wout[(int64_t)cidx[p] * s + c]);
-    return v;
-  }
-  return local < k ? Wout[R * s + c] : Xsub[(int64_t)rows[R] * s + c];
-}
-
 // One tile: MF_TILE output rows x MF_TK reduction indices of
-//   forward : t = X_t b_P      (X_t column-major f x k)
-//   backward: x = X_t^T v      (X_t^T column-major k x f, v = [y_P; x_U])
+//   forward : t = X_t b_P      (X_t column-major f x k); b_P at a pivot row
+//             is the sub-vector entry plus the children's update vectors
+//             that land on it (extend-add, child order)
+//   backward: x = X_t^T v      (X_t^T column-major k x f, v = [y_P; x_U]:
+//             y_P kept in Wout by the forward sweep, x_U the final values of
+//             the ancestors' pivots in the sub-vector)
 // A row block covered by one tile (slot < 0) applies the epilogue directly;
 // otherwise the tile writes a partial result to its slot of P and the row
 // block's partials are summed in a fixed order by k_mf_reduce. Epilogue:
@@ -266,18 +253,49 @@ __device__ __forceinline__ V sweep_input(int64_t R, int local, int k, int c, int
 // (NT apart, so a warp reads 32 consecutive factor entries per column) and
 // the s right-hand sides as register accumulators; chunks of the input vector
 // are staged in shared memory and read as broadcasts.
-template <typename V, int S, int R, int NT, int G, bool FWD>
-__global__ void __launch_bounds__(NT * G) k_mf_tile(const int4* __restrict__ tiles, const int* __restrict__ kk,
-                                                    const int* __restrict__ ff, const int64_t* __restrict__ rowoff,
-                                                    const int64_t* __restrict__ Moff, const V* __restrict__ M,
-                                                    const int* __restrict__ rows, const int64_t* __restrict__ cptr,
-                                                    const int* __restrict__ cidx, const int64_t* __restrict__ Doff,
-                                                    const V* __restrict__ Dinv, V* __restrict__ Xsub,
-                                                    V* __restrict__ Wout, V* __restrict__ P, int s) {
-  static_assert(NT * R == MF_TILE, "tile height");
+__device__ __forceinline__ void cp_async_elem(void* dst_smem, const float2* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(void* dst_smem, const double2* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// columns of the factor tile per asynchronous chunk (two chunks in flight)
+template <typename V>
+struct TileChunk {
+  static constexpr int K = sizeof(V) == 8 ? 16 : 8;
+};
+
+template <typename V, int S>
+static constexpr size_t tile_smem_bytes() {
+  return sizeof(V) * ((size_t)MF_TK * S + 2 * (size_t)TileChunk<V>::K * MF_TILE);
+}
+
+// Each thread owns one output row (MF_TILE threads) and keeps the s
+// right-hand sides as register accumulators. The tile's input rows are
+// staged once in shared memory (read as broadcasts); the factor tile streams
+// through a two-chunk shared-memory ring filled by cp.async (a warp copies 32
+// consecutive entries of one factor column), so the next chunk's loads are in
+// flight while the current one is consumed.
+template <typename V, int S, bool FWD>
+__global__ void __launch_bounds__(MF_TILE) k_mf_tile(const int4* __restrict__ tiles, const int* __restrict__ kk,
+                                                     const int* __restrict__ ff, const int64_t* __restrict__ rowoff,
+                                                     const int64_t* __restrict__ Moff, const V* __restrict__ M,
+                                                     const int* __restrict__ rows, const int64_t* __restrict__ cptr,
+                                                     const int* __restrict__ cidx, const int64_t* __restrict__ Doff,
+                                                     const V* __restrict__ Dinv, V* __restrict__ Xsub,
+                                                     V* __restrict__ Wout, V* __restrict__ P, int s) {
+  constexpr int KCH = TileChunk<V>::K;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V(*bs)[S] = reinterpret_cast<V(*)[S]>(smem_raw);                            // [MF_TK][S] tile input
-  V(*red)[S] = reinterpret_cast<V(*)[S]>(smem_raw + sizeof(V) * MF_TK * S);  // [(G-1) MF_TILE][S]
+  V(*bs)[S] = reinterpret_cast<V(*)[S]>(smem_raw);                                       // [MF_TK][S]
+  V(*mb)[MF_TILE] = reinterpret_cast<V(*)[MF_TILE]>(smem_raw + sizeof(V) * MF_TK * S);  // [2 KCH][MF_TILE]
   const int4 tile = tiles[blockIdx.x];
   const int t = tile.x, r0 = tile.y, c0 = tile.z, slot = tile.w;
   const int f = ff[t], k = kk[t];
@@ -288,117 +306,97 @@ __global__ void __launch_bounds__(NT * G) k_mf_tile(const int4* __restrict__ til
   const int kstop = min(kend, c0 + MF_TK);
   const V* Mt = M + Moff[t];
   const int64_t ro = rowoff[t];
-  const int grp = threadIdx.x / NT, tid = threadIdx.x % NT;
+  const int tid = threadIdx.x;
   const int lmax = max(0, kstop - kbeg);
-  const int per = (lmax + G - 1) / G;
-  const int l0 = min(lmax, grp * per), l1 = min(lmax, l0 + per);
-  const V* mrow[R];
-  bool act[R];
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    const int rr = r0 + tid + q * NT;
-    act[q] = rr < nout;
-    mrow[q] = Mt + (act[q] ? rr : 0) + (int64_t)kbeg * ld;
+  const int rr = r0 + tid;
+  const bool act = rr < nout;
+  const V* mcol = Mt + (act ? rr : 0) + (int64_t)kbeg * ld;
+  const int nch = (lmax + KCH - 1) / KCH;
+  // chunk 0 in flight while the input rows are staged
+  if (nch > 0) {
+    const int cn = min(KCH, lmax);
+    if (act)
+      for (int j = 0; j < cn; ++j) cp_async_elem(&mb[j][tid], mcol + (int64_t)j * ld);
   }
-  // first factor entries in flight while the inputs are staged
-  constexpr int PF = 8;
-  V pre[PF][R];
+  cp_async_commit();
+  for (int l = tid; l < lmax; l += MF_TILE) {
+    const int64_t R = ro + kbeg + l;
+    const int local = kbeg + l;
+    V v[S];
+    const V* src = (FWD || local >= k) ? Xsub + (int64_t)rows[R] * s : Wout + R * s;
 #pragma unroll
-  for (int u = 0; u < PF; ++u)
-#pragma unroll
-    for (int q = 0; q < R; ++q)
-      pre[u][q] = (act[q] && l0 + u < l1) ? mrow[q][(int64_t)(l0 + u) * ld] : mk2((decltype(V::x))0, (decltype(V::x))0);
-  for (int i = threadIdx.x; i < lmax * S; i += NT * G) {
-    const int l = i / S, c = i % S;
-    V v = mk2((decltype(V::x))0, (decltype(V::x))0);
-    if (c < s) v = sweep_input<V, FWD>(ro + kbeg + l, kbeg + l, k, c, s, rows, cptr, cidx, Xsub, Wout);
-    bs[l][c] = v;
-  }
-  __syncthreads();
-  V acc[R][S];
-#pragma unroll
-  for (int q = 0; q < R; ++q)
-#pragma unroll
-    for (int c = 0; c < S; ++c) acc[q][c] = mk2((decltype(V::x))0, (decltype(V::x))0);
-  {
-    // the G thread groups split the tile's reduction range
-#pragma unroll
-    for (int u = 0; u < PF; ++u) {
-      if (l0 + u >= l1) break;
-#pragma unroll
-      for (int c = 0; c < S; ++c) {
-        const V b = bs[l0 + u][c];
-#pragma unroll
-        for (int q = 0; q < R; ++q) acc[q][c] = c_fma(pre[u][q], b, acc[q][c]);
-      }
-    }
-#pragma unroll 8
-    for (int l = l0 + PF; l < l1; ++l) {
-      V m[R];
-#pragma unroll
-      for (int q = 0; q < R; ++q)
-        m[q] = act[q] ? mrow[q][(int64_t)l * ld] : mk2((decltype(V::x))0, (decltype(V::x))0);
-#pragma unroll
-      for (int c = 0; c < S; ++c) {
-        const V b = bs[l][c];
-#pragma unroll
-        for (int q = 0; q < R; ++q) acc[q][c] = c_fma(m[q], b, acc[q][c]);
-      }
-    }
-  }
-  if (G > 1) {
-    if (grp > 0) {
-#pragma unroll
-      for (int q = 0; q < R; ++q)
-#pragma unroll
-        for (int c = 0; c < S; ++c) red[(grp - 1) * MF_TILE + tid + q * NT][c] = acc[q][c];
-    }
-    __syncthreads();
-    if (grp > 0) return;
-#pragma unroll
-    for (int g = 1; g < G; ++g)
-#pragma unroll
-      for (int q = 0; q < R; ++q)
-#pragma unroll
-        for (int c = 0; c < S; ++c) acc[q][c] = c_add(acc[q][c], red[(g - 1) * MF_TILE + tid + q * NT][c]);
-  }
-  if (slot >= 0) {
-    V* out = P + (int64_t)slot * MF_TILE * s;
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const int i = tid + q * NT;
-#pragma unroll
-      for (int c = 0; c < S; ++c)
-        if (c < s) out[i * s + c] = acc[q][c];
-    }
-    return;
-  }
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    const int rr = r0 + tid + q * NT;
-    if (rr >= nout) continue;
-    const int64_t Rg = ro + rr;
+    for (int c = 0; c < S; ++c) v[c] = c < s ? src[c] : mk2((decltype(V::x))0, (decltype(V::x))0);
     if (FWD) {
-      if (rr < k) {
-        const V di = Dinv[Doff[t] + rr];
+      const int64_t pe = cptr[R + 1];
+      for (int64_t p = cptr[R]; p < pe; ++p) {
+        const V* w = Wout + (int64_t)cidx[p] * s;
 #pragma unroll
         for (int c = 0; c < S; ++c)
-          if (c < s) Wout[Rg * s + c] = c_mul(acc[q][c], di);
-      } else {
-#pragma unroll
-        for (int c = 0; c < S; ++c) {
-          if (c >= s) continue;
-          V a = acc[q][c];
-          for (int64_t p = cptr[Rg]; p < cptr[Rg + 1]; ++p) a = c_add(a, Wout[(int64_t)cidx[p] * s + c]);
-          Wout[Rg * s + c] = a;
-        }
+          if (c < s) v[c] = c_add(v[c], w[c]);
       }
-    } else {
-      V* xo = Xsub + (int64_t)rows[Rg] * s;
+    }
+#pragma unroll
+    for (int c = 0; c < S; ++c) bs[l][c] = v[c];
+  }
+  V acc[S];
+#pragma unroll
+  for (int c = 0; c < S; ++c) acc[c] = mk2((decltype(V::x))0, (decltype(V::x))0);
+  for (int ch = 0; ch < nch; ++ch) {
+    // issue chunk ch + 1 into the other half of the ring, then wait for ch
+    if (ch + 1 < nch) {
+      const int j0 = (ch + 1) * KCH, cn = min(KCH, lmax - j0);
+      const int half = ((ch + 1) & 1) * KCH;
+      if (act)
+        for (int j = 0; j < cn; ++j) cp_async_elem(&mb[half + j][tid], mcol + (int64_t)(j0 + j) * ld);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    const int half = (ch & 1) * KCH;
+    const int j0 = ch * KCH, cn = min(KCH, lmax - j0);
+#pragma unroll 4
+    for (int j = 0; j < cn; ++j) {
+      const V m = mb[half + j][tid];
+#pragma unroll
+      for (int c = 0; c < S; ++c) acc[c] = c_fma(m, bs[j0 + j][c], acc[c]);
+    }
+    __syncthreads();  // the half just read is refilled in the next iteration
+  }
+  cp_async_wait<0>();
+  if (slot >= 0) {
+    V* out = P + ((int64_t)slot * MF_TILE + tid) * s;
+#pragma unroll
+    for (int c = 0; c < S; ++c)
+      if (c < s) out[c] = acc[c];
+    return;
+  }
+  if (!act) return;
+  const int64_t Rg = ro + rr;
+  if (FWD) {
+    if (rr < k) {
+      const V di = Dinv[Doff[t] + rr];
 #pragma unroll
       for (int c = 0; c < S; ++c)
-        if (c < s) xo[c] = acc[q][c];
+        if (c < s) Wout[Rg * s + c] = c_mul(acc[c], di);
+    } else {
+      // parent update: the children's update vectors landing on this row,
+      // one contiguous row of s values per contribution
+      const int64_t pe = cptr[Rg + 1];
+      for (int64_t p = cptr[Rg]; p < pe; ++p) {
+        const V* w = Wout + (int64_t)cidx[p] * s;
+#pragma unroll
+        for (int c = 0; c < S; ++c)
+          if (c < s) acc[c] = c_add(acc[c], w[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < S; ++c)
+        if (c < s) Wout[Rg * s + c] = acc[c];
     }
+  } else {
+    V* xo = Xsub + (int64_t)rows[Rg] * s;
+#pragma unroll
+    for (int c = 0; c < S; ++c)
+      if (c < s) xo[c] = acc[c];
   }
 }
 
@@ -440,14 +438,9 @@ __global__ void k_mf_reduce(const int4* __restrict__ rblocks, int nrb, const int
 
 static inline unsigned blocks_for(int64_t work, int b) { return (unsigned)((work + b - 1) / b); }
 
-template <typename V, int S, int R, int NT, int G>
-static constexpr size_t tile_smem() {
-  return sizeof(V) * (size_t)S * (MF_TK + (G - 1) * MF_TILE);
-}
-
-template <typename V, int S, int R, int NT, int G>
+template <typename V, int S>
 static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
-  const size_t shm = tile_smem<V, S, R, NT, G>();
+  const size_t shm = tile_smem_bytes<V, S>();
   V* Wout = (V*)mf.Wout;
   V* P = (V*)mf.P;
   const V* M = (const V*)mf.M;
@@ -456,8 +449,8 @@ static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
   for (int l = 0; l < mf.nlevels; ++l) {
     const int tb = mf.ftile_ptr_h[l], te = mf.ftile_ptr_h[l + 1];
     if (te > tb)
-      { k_mf_tile<V, S, R, NT, G, true><<<te - tb, NT * G, shm, st>>>(mf.ftiles + tb, mf.k, mf.f, mf.rowoff, mf.Moff, M, mf.rows,
-                                                           mf.cptr, mf.cidx, mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
+      { k_mf_tile<V, S, true><<<te - tb, MF_TILE, shm, st>>>(mf.ftiles + tb, mf.k, mf.f, mf.rowoff, mf.Moff, M, mf.rows,
+                                                             mf.cptr, mf.cidx, mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
     const int rb = mf.frb_ptr_h[l], re = mf.frb_ptr_h[l + 1];
     if (re > rb)
       { k_mf_reduce<V, true><<<blocks_for((int64_t)(re - rb) * MF_TILE * s, 256), 256, 0, st>>>(
@@ -466,8 +459,8 @@ static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
   for (int l = mf.nlevels - 1; l >= 0; --l) {
     const int tb = mf.btile_ptr_h[l], te = mf.btile_ptr_h[l + 1];
     if (te > tb)
-      { k_mf_tile<V, S, R, NT, G, false><<<te - tb, NT * G, shm, st>>>(mf.btiles + tb, mf.k, mf.f, mf.rowoff, mf.Moff, MT,
-                                                            mf.rows, mf.cptr, mf.cidx, mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
+      { k_mf_tile<V, S, false><<<te - tb, MF_TILE, shm, st>>>(mf.btiles + tb, mf.k, mf.f, mf.rowoff, mf.Moff, MT,
+                                                              mf.rows, mf.cptr, mf.cidx, mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
     const int rb = mf.brb_ptr_h[l], re = mf.brb_ptr_h[l + 1];
     if (re > rb)
       { k_mf_reduce<V, false><<<blocks_for((int64_t)(re - rb) * MF_TILE * s, 256), 256, 0, st>>>(
@@ -477,33 +470,30 @@ static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
 
 // Opt the tile kernels into their dynamic shared memory once, outside any
 // stream capture (called from the factorisation).
-template <typename V, int S, int R, int NT, int G>
+template <typename V, int S>
 static void tile_attrs() {
-  const int shm = (int)tile_smem<V, S, R, NT, G>();
-  cudaFuncSetAttribute(k_mf_tile<V, S, R, NT, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
-  cudaFuncSetAttribute(k_mf_tile<V, S, R, NT, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+  const int shm = (int)tile_smem_bytes<V, S>();
+  cudaFuncSetAttribute(k_mf_tile<V, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+  cudaFuncSetAttribute(k_mf_tile<V, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
 }
 
-// (S, R, NT, G): right-hand sides in registers, rows per thread, threads per
-// group (NT * R = 128 rows), groups splitting the reduction range
-#define HZ_TILE_CONFIGS(X) \
-  X(1, 1, 128, 1) X(2, 1, 128, 1) X(4, 1, 128, 1) X(8, 1, 128, 1) X(16, 1, 128, 1) X(32, 1, 128, 1) X(64, 1, 128, 1)
+#define HZ_TILE_WIDTHS(X) X(1) X(2) X(4) X(8) X(16) X(32) X(64)
 
 template <typename V>
 static void tile_attrs_all() {
-#define HZ_ATTR(S, R, NT, G) tile_attrs<V, S, R, NT, G>();
-  HZ_TILE_CONFIGS(HZ_ATTR)
+#define HZ_ATTR(S) tile_attrs<V, S>();
+  HZ_TILE_WIDTHS(HZ_ATTR)
 #undef HZ_ATTR
 }
 
 template <typename V>
 static void solve_dispatch(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
-#define HZ_CASE(S, R, NT, G)                         \
-  if (s <= S) {                                      \
-    solve_impl<V, S, R, NT, G>(mf, Xsub, s, st);     \
-    return;                                          \
+#define HZ_CASE(S)                       \
+  if (s <= S) {                          \
+    solve_impl<V, S>(mf, Xsub, s, st);   \
+    return;                              \
   }
-  HZ_TILE_CONFIGS(HZ_CASE)
+  HZ_TILE_WIDTHS(HZ_CASE)
 #undef HZ_CASE
 }
 
