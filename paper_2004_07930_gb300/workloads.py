@@ -332,3 +332,39 @@ def random_rhs(n, ns, seed):
     """Seeded complex normal block [ns, n] (test right-hand sides)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.standard_normal((ns, n)) + 1j * rng.standard_normal((ns, n))
+
+
+# ----------------------------------------------------------------------------
+# FWI inputs: acquisition and a perturbed "true" model
+# ----------------------------------------------------------------------------
+def gaussian_anomaly(prob, amp=0.03, radius=None, seed=0):
+    """Per-element velocity of `prob` times (1 + sign * amp * exp(-|x-c|^2 /
+    (2 radius^2))): one Gaussian anomaly of +-amp (sign and centre c drawn
+    from PCG64(seed); c uniform in the middle half of the box); radius
+    defaults to 1/8 of the smallest box side."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    fine = prob["fine"]
+    lo = np.array([fine["xs"][0], fine["ys"][0], fine["zs"][0]])
+    hi = np.array([fine["xs"][-1], fine["ys"][-1], fine["zs"][-1]])
+    sign = 1.0 if rng.uniform() < 0.5 else -1.0
+    c = lo + (hi - lo) * rng.uniform(0.25, 0.75, size=3)
+    r = (hi - lo).min() / 8.0 if radius is None else radius
+    x = centroids(fine["xyz"], fine["tets"])
+    return prob["velocity"] * (1.0 + sign * amp * np.exp(-((x - c) ** 2).sum(axis=1) / (2.0 * r * r)))
+
+
+def fwi_acquisition(prob, nsrc_xy=(8, 4), nrec_xy=(20, 20), depth=100.0, margin=0.05):
+    """Sources on a regular nsrc_xy grid and receivers on a regular nrec_xy
+    grid, both at `depth` below the top face, inset by `margin` of the box."""
+    fine = prob["fine"]
+    x0, x1 = fine["xs"][0], fine["xs"][-1]
+    y0, y1 = fine["ys"][0], fine["ys"][-1]
+    z = fine["zs"][0] + depth
+
+    def grid(nx, ny):
+        xs = np.linspace(x0 + margin * (x1 - x0), x1 - margin * (x1 - x0), nx)
+        ys = np.linspace(y0 + margin * (y1 - y0), y1 - margin * (y1 - y0), ny)
+        X, Y = np.meshgrid(xs, ys, indexing="ij")
+        return np.stack([X.ravel(), Y.ravel(), np.full(X.size, z)], axis=1)
+
+    return grid(*nsrc_xy), grid(*nrec_xy)
