@@ -191,6 +191,62 @@ int hz_profile_begin(hz_ctx* ctx);
 /* Synchronise the stream, stop recording and write up to `cap` phases. */
 int hz_profile_end(hz_ctx* ctx, hz_phase_time* out, int32_t cap, int32_t* count);
 
+/* Continuous batching of point-source requests on one context (one mesh and
+ * frequency; the factors stay resident). Multi-RHS processing is the paper's
+ * motivation (Sec. "Introduction", Sec. "Conclusion"); the request loop
+ * itself has no counterpart in the paper.
+ * A server owns `slots` right-hand-side columns (<= max_block) and allocates
+ * its blocks once, in hz_server_create. Requests (several sources each) are
+ * queued by hz_server_submit; every hz_server_step admits queued sources
+ * into free slots, runs one FGMRES restart cycle on all occupied slots
+ * together, and retires the slots whose true residual reached rtol (or that
+ * used maxit iterations). Each column has its own Krylov space and its
+ * arithmetic does not depend on the other columns, so a request's
+ * wavefields are the same alone and in any mix. Finished requests are
+ * listed in done_ids (up to cap per step) and read once with
+ * hz_server_fetch (u [ns][n][2] host doubles; HZ_ENOTCONV if a column stopped
+ * at maxit). Steps of servers of different contexts may be interleaved; a
+ * server and its context are not thread-safe. Errors: HZ_EINVAL (bad
+ * argument, unknown or unfinished request, duplicate id, source outside the
+ * mesh), HZ_ENOMEM, HZ_ECUDA. */
+typedef struct hz_server hz_server;
+int hz_server_create(hz_ctx* ctx, int32_t slots, hz_server** out);
+int hz_server_submit(hz_server* srv, int64_t request_id, const double* src_xyz, const double* src_amp, int32_t ns);
+int hz_server_step(hz_server* srv, int64_t* done_ids, int32_t cap, int32_t* ndone);
+int hz_server_fetch(hz_server* srv, int64_t request_id, double* u, hz_stats* stats);
+int hz_server_pending(const hz_server* srv, int32_t* queued, int32_t* active);
+void hz_server_free(hz_server* srv);
+
+/* Receiver sampling operator P of the FWI misfit: the value at x_k of the
+ * P3 field u is sum_i w[k][i] u[idx[k][i]], with phi evaluated in the
+ * lowest-index element containing x_k (the rule of the point-source load, so
+ * P^T a is the load of point sources of amplitudes a at the receivers).
+ *   rec_xyz [nr][3]; idx [nr][20] dofs (-1: Dirichlet dof or zero weight);
+ *   w [nr][20]. Host only; HZ_EINVAL if a receiver lies outside the mesh. */
+int hz_receiver_operator(const hz_ctx* ctx, const double* rec_xyz, int32_t nr, int32_t* idx, double* w);
+
+/* Least-squares FWI misfit and its gradient with respect to the squared
+ * slowness m_e = 1/c_e^2 of every element, by the adjoint-state method. The
+ * paper's solver is the forward engine of frequency-domain FWI (Sec.
+ * "Introduction"); it prints no gradient, the formula is the standard one:
+ *   chi = 1/2 sum_s sum_k |(P u_s)_k - d_{s,k}|^2,  A u_s = F_s (point sources),
+ *   A lambda_s = P^T conj(P u_s - d_s)   (A is complex symmetric),
+ *   grad_e = -Re sum_s lambda_s^T (dA/dm_e) u_s,
+ *   dA/dm_e = -omega^2 M_e - (i omega / (2 sqrt(m_e))) sum_{Robin faces f of e} B_f
+ * on the element's non-Dirichlet dofs. Forward and adjoint solves use the
+ * context's factors and options (2 ns solves).
+ *   src_xyz [ns][3], src_amp [ns][2]: point sources as in hz_solve
+ *   rec_xyz [nr][3]: receivers (hz_receiver_operator)
+ *   d_obs   [ns][nr][2] observed data, host; NULL = zero data
+ *   chi     misfit (may be NULL); grad [ne] host output
+ *   d_syn   [ns][nr][2] host output P u_s (may be NULL)
+ *   stats   iterations = max over all solves, ncols = 2 ns (may be NULL)
+ * The first call uploads per-element data (dofs, volumes, Robin face areas,
+ * m) that the context then keeps. Returns HZ_ENOTCONV if a solve stopped at
+ * maxit (outputs computed from the last iterates). */
+int hz_fwi_gradient(hz_ctx* ctx, const double* src_xyz, const double* src_amp, int32_t ns, const double* rec_xyz,
+                    int32_t nr, const double* d_obs, double* chi, double* grad, double* d_syn, hz_stats* stats);
+
 /* Host copy of A in CSR form: rowptr [n+1], col [nnz], val [nnz][2]. */
 int hz_matrix_csr(const hz_ctx* ctx, int64_t* rowptr, int32_t* col, double* val);
 

@@ -15,6 +15,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <deque>
+#include <map>
 #include <memory>
 #include <numeric>
 #include <string>
@@ -530,6 +532,14 @@ struct hz_ctx {
   int* d_srcidx = nullptr;
   double2* d_srcval = nullptr;
   int src_cap = 0;
+  // per-element data of the FWI gradient (uploaded by the first hz_fwi_gradient call)
+  double omega = 0;
+  std::vector<double> mvals;
+  bool fwi_ready = false;
+  int* d_fwi_l2g = nullptr;        // [ne][20], -1 on Dirichlet dofs
+  double* d_fwi_vol = nullptr;     // [ne]
+  double* d_fwi_farea = nullptr;   // [ne][4], area of Robin faces, 0 elsewhere
+  double* d_fwi_m = nullptr;       // [ne]
 };
 
 namespace {
@@ -772,13 +782,53 @@ void apply_prec(hz_ctx* c, const double2* V, double2* Zout, int s) {
   apply_oras(c->lf, c->T, Zout, c->Q, c->Xsub, s, st, &c->prof, gf);      // z = M1^{-1} t + q
 }
 
+// One restart cycle of flexible GMRES on the block: Krylov space from the
+// current residual c->R, at most max_its iterations (fewer when every column
+// has converged or broken down), then X += Zk y. K.tol must hold the
+// per-column absolute tolerances. Returns the iterations done.
+int fgmres_cycle(hz_ctx* c, int s, int max_its) {
+  cudaStream_t st = c->st;
+  const int64_t n = c->space.n;
+  DevKrylov& K = c->Kout;
+  K.s = s;
+  const int m = std::min(c->opt.restart, max_its);
+  const int64_t vs = n * s;
+  krylov_start(K, c->R, st);
+  int its = 0;
+  for (int j = 0; j < m; ++j) {
+    apply_prec(c, (double2*)K.V + j * vs, (double2*)K.Zk + j * vs, s);
+    spmm_A(c, (double2*)K.Zk + j * vs, (double2*)K.W, nullptr, s, 0);
+    int id = c->prof.begin(PH_ARNOLDI, st);
+    krylov_arnoldi(K, j, st);
+    // two CGS passes (dots + update) over V_0..j and W, a norm and a scale
+    c->prof.end(id, st, 2.0 * 2.0 * 8.0 * n * (j + 1) * s, 16.0 * n * s * (4.0 * (j + 1) + 6.0));
+    ++its;
+    CK(cudaMemcpyAsync(c->h_done, K.done, s * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    bool alldone = true;
+    for (int q = 0; q < s; ++q) alldone &= c->h_done[q] != 0;
+    if (alldone) break;
+  }
+  krylov_update(K, c->X, st);
+  return its;
+}
+
+// True residual R = B - A X and its column norms (host, into c->h_res).
+void true_residual(hz_ctx* c, int s) {
+  cudaStream_t st = c->st;
+  const int64_t n = c->space.n;
+  spmm_A(c, c->X, c->R, c->B, s, 1);
+  column_norms(c->R, n, s, c->rnorm, c->Kout, st);
+  CK(cudaMemcpyAsync(c->h_res, c->rnorm, s * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+}
+
 // Flexible GMRES on the block c->B (n x s, row-major); solution in c->X.
 int fgmres(hz_ctx* c, int s, hz_stats* stats) {
   cudaStream_t st = c->st;
   const int64_t n = c->space.n;
   DevKrylov& K = c->Kout;
   K.s = s;
-  const int m = c->opt.restart;
   const int64_t vs = n * s;
   axpy_cols_zero(c->X, vs, st);
   column_norms(c->B, n, s, c->bnorm, K, st);
@@ -795,27 +845,8 @@ int fgmres(hz_ctx* c, int s, hz_stats* stats) {
   bool all_conv = false;
   double maxrel = 0.0;
   while (true) {
-    krylov_start(K, c->R, st);
-    for (int j = 0; j < m && its < c->opt.maxit; ++j) {
-      apply_prec(c, (double2*)K.V + j * vs, (double2*)K.Zk + j * vs, s);
-      spmm_A(c, (double2*)K.Zk + j * vs, (double2*)K.W, nullptr, s, 0);
-      int id = c->prof.begin(PH_ARNOLDI, st);
-      krylov_arnoldi(K, j, st);
-      // two CGS passes (dots + update) over V_0..j and W, a norm and a scale
-      c->prof.end(id, st, 2.0 * 2.0 * 8.0 * n * (j + 1) * s,
-                  16.0 * n * s * (4.0 * (j + 1) + 6.0));
-      ++its;
-      CK(cudaMemcpyAsync(c->h_done, K.done, s * sizeof(int), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      bool alldone = true;
-      for (int q = 0; q < s; ++q) alldone &= c->h_done[q] != 0;
-      if (alldone) break;
-    }
-    krylov_update(K, c->X, st);
-    spmm_A(c, c->X, c->R, c->B, s, 1);  // true residual R = B - A X
-    column_norms(c->R, n, s, c->rnorm, K, st);
-    CK(cudaMemcpyAsync(c->h_res, c->rnorm, s * sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    its += fgmres_cycle(c, s, c->opt.maxit - its);
+    true_residual(c, s);
     all_conv = true;
     maxrel = 0.0;
     for (int q = 0; q < s; ++q) {
@@ -935,6 +966,8 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
     for (int64_t v : pc)
       if (v == 0) throw HzError{HZ_EINVAL, "empty subdomain in the partition"};
     const double omega = 2.0 * M_PI * freq_hz;
+    c->omega = omega;
+    c->mvals = mvals;
     c->user_st = (cudaStream_t)stream;
     CK(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
@@ -1265,3 +1298,430 @@ const char* hz_strerror(int code) {
 const char* hz_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Continuous batching of point-source requests (hz_server_*)
+// ---------------------------------------------------------------------------
+namespace {
+
+// right-hand-side entries of one point source in column col of an [n][s] block
+void point_source_entries(const hz_ctx* c, const double* xyz, const double* amp, int s, int col,
+                          std::vector<int>& idx, std::vector<double2>& val) {
+  int64_t e = -1;
+  double lam[4];
+  locate_points(c->fine, xyz, 1, &e, lam);
+  if (e < 0) throw HzError{HZ_EINVAL, "source outside the mesh"};
+  double phi[NLOC];
+  p3_basis(lam, phi);
+  for (int i = 0; i < NLOC; ++i) {
+    const int64_t g = c->space.l2g[NLOC * e + i];
+    if (c->space.dirichlet[g]) continue;
+    idx.push_back((int)(g * s + col));
+    val.push_back(make_double2(amp[0] * phi[i], amp[1] * phi[i]));
+  }
+}
+
+void upload_sources(hz_ctx* c, const std::vector<int>& idx, const std::vector<double2>& val) {
+  cudaStream_t st = c->st;
+  if ((int)idx.size() > c->src_cap) {
+    CK(cudaStreamSynchronize(st));
+    if (c->d_srcidx) cudaFree(c->d_srcidx);
+    if (c->d_srcval) cudaFree(c->d_srcval);
+    c->d_srcidx = nullptr;
+    c->d_srcval = nullptr;
+    c->src_cap = 0;
+    CK(cudaMalloc(&c->d_srcidx, idx.size() * sizeof(int)));
+    CK(cudaMalloc(&c->d_srcval, val.size() * sizeof(double2)));
+    c->src_cap = (int)idx.size();
+  }
+  CK(cudaMemcpyAsync(c->d_srcidx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(c->d_srcval, val.data(), val.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+}
+
+}  // namespace
+
+struct hz_server {
+  hz_ctx* c = nullptr;
+  int s = 0;
+  struct Col {
+    int64_t req;
+    int idx;
+  };
+  struct Req {
+    int ns = 0, remaining = 0, iterations = 0, converged = 1;
+    double maxrel = 0.0;
+    std::vector<double> xyz, amp;
+    std::vector<double2> u;  // [ns][n] results
+  };
+  std::deque<Col> queue;
+  std::vector<Col> slot;  // req = -1: free
+  std::vector<int> slot_its;
+  std::vector<double> slot_bn;
+  std::map<int64_t, Req> reqs;
+  // the slots' right-hand sides, iterates and residuals persist across
+  // steps: the server owns them and lends them to the context for each step
+  double2 *B = nullptr, *X = nullptr, *R = nullptr, *d_col = nullptr;
+  ~hz_server() {
+    if (c) cudaStreamSynchronize(c->st);
+    for (double2* p : {B, X, R, d_col})
+      if (p) cudaFree(p);
+  }
+  struct Lend {  // swaps the server's blocks into the context for one step
+    hz_ctx* c;
+    double2 *B, *X, *R;
+    explicit Lend(hz_server* v) : c(v->c), B(v->c->B), X(v->c->X), R(v->c->R) {
+      c->B = v->B;
+      c->X = v->X;
+      c->R = v->R;
+    }
+    ~Lend() {
+      c->B = B;
+      c->X = X;
+      c->R = R;
+    }
+  };
+};
+
+extern "C" int hz_server_create(hz_ctx* c, int32_t slots, hz_server** out) {
+  if (!c || !out || slots < 1 || slots > c->opt.max_block) return fail(HZ_EINVAL, "bad argument");
+  *out = nullptr;
+  return guarded([&]() -> int {
+    std::unique_ptr<hz_server> v(new hz_server());
+    v->c = c;
+    v->s = slots;
+    join_user(c);
+    ensure_workspace(c, slots);
+    v->slot.assign(slots, hz_server::Col{-1, 0});
+    v->slot_its.assign(slots, 0);
+    v->slot_bn.assign(slots, 0.0);
+    const int64_t vs = c->space.n * slots;
+    for (double2** p : {&v->B, &v->X, &v->R}) {
+      if (cudaMalloc(p, vs * sizeof(double2)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        throw HzError{HZ_ENOMEM, "server block allocation failed"};
+      }
+      axpy_cols_zero(*p, vs, c->st);
+    }
+    if (cudaMalloc(&v->d_col, c->space.n * sizeof(double2)) != cudaSuccess) {
+      cudaGetLastError();
+      v->d_col = nullptr;
+      throw HzError{HZ_ENOMEM, "server column allocation failed"};
+    }
+    check_launch();
+    CK(cudaStreamSynchronize(c->st));
+    *out = v.release();
+    return HZ_OK;
+  });
+}
+
+extern "C" int hz_server_submit(hz_server* v, int64_t id, const double* src_xyz, const double* src_amp, int32_t ns) {
+  if (!v || !src_xyz || !src_amp || ns < 1) return fail(HZ_EINVAL, "bad argument");
+  if (v->reqs.count(id)) return fail(HZ_EINVAL, "request id already in use");
+  return guarded([&]() -> int {
+    hz_server::Req r;
+    r.ns = r.remaining = ns;
+    r.xyz.assign(src_xyz, src_xyz + 3 * (size_t)ns);
+    r.amp.assign(src_amp, src_amp + 2 * (size_t)ns);
+    std::vector<int64_t> elem(ns);
+    std::vector<double> lam(4 * (size_t)ns);
+    locate_points(v->c->fine, r.xyz.data(), ns, elem.data(), lam.data());
+    for (int q = 0; q < ns; ++q)  // reject sources outside the mesh up front
+      if (elem[q] < 0) throw HzError{HZ_EINVAL, "source outside the mesh"};
+    v->reqs.emplace(id, std::move(r));
+    for (int q = 0; q < ns; ++q) v->queue.push_back(hz_server::Col{id, q});
+    return HZ_OK;
+  });
+}
+
+extern "C" int hz_server_step(hz_server* v, int64_t* done_ids, int32_t cap, int32_t* ndone) {
+  if (!v || !ndone || (cap > 0 && !done_ids)) return fail(HZ_EINVAL, "bad argument");
+  *ndone = 0;
+  return guarded([&]() -> int {
+    hz_ctx* c = v->c;
+    cudaStream_t st = c->st;
+    const int s = v->s;
+    const int64_t n = c->space.n;
+    join_user(c);
+    ensure_workspace(c, s);
+    hz_server::Lend lend(v);
+    // admit queued columns into free slots
+    std::vector<int> idx;
+    std::vector<double2> val;
+    for (int q = 0; q < s && !v->queue.empty(); ++q) {
+      if (v->slot[q].req >= 0) continue;
+      const hz_server::Col col = v->queue.front();
+      v->queue.pop_front();
+      const hz_server::Req& r = v->reqs.at(col.req);
+      v->slot[q] = col;
+      v->slot_its[q] = 0;
+      point_source_entries(c, &r.xyz[3 * (size_t)col.idx], &r.amp[2 * (size_t)col.idx], s, q, idx, val);
+    }
+    int active = 0;
+    for (int q = 0; q < s; ++q) active += v->slot[q].req >= 0;
+    if (active == 0) return HZ_OK;
+    if (!idx.empty()) {
+      upload_sources(c, idx, val);
+      scatter_point_sources(c->B, n, s, c->d_srcidx, c->d_srcval, (int)idx.size(), st);
+      for (int q = 0; q < s; ++q)  // new columns start from X = 0, so R = B
+        if (v->slot[q].req >= 0 && v->slot_its[q] == 0) col_copy(c->B, c->R, n, s, q, st);
+    }
+    // per-slot tolerances (free slots: 0; their zero residual counts as done)
+    column_norms(c->B, n, s, c->bnorm, c->Kout, st);
+    CK(cudaMemcpyAsync(c->h_res, c->bnorm, s * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::vector<double> tol(s);
+    for (int q = 0; q < s; ++q) {
+      v->slot_bn[q] = c->h_res[q];
+      tol[q] = v->slot[q].req >= 0 ? c->opt.rtol * v->slot_bn[q] : 0.0;
+    }
+    CK(cudaMemcpyAsync(c->Kout.tol, tol.data(), s * sizeof(double), cudaMemcpyHostToDevice, st));
+    // one restart cycle for every slot, then the true residuals
+    int maxleft = 1;
+    for (int q = 0; q < s; ++q)
+      if (v->slot[q].req >= 0) maxleft = std::max(maxleft, c->opt.maxit - v->slot_its[q]);
+    fgmres_cycle(c, s, std::min(c->opt.restart, maxleft));
+    std::vector<int> kc(s);  // Arnoldi steps each column accepted in this cycle
+    CK(cudaMemcpyAsync(kc.data(), c->Kout.kc, s * sizeof(int), cudaMemcpyDeviceToHost, st));
+    true_residual(c, s);
+    check_launch();
+    for (int q = 0; q < s; ++q) {
+      if (v->slot[q].req < 0) continue;
+      v->slot_its[q] += std::max(kc[q], 1);  // at least one: a stalled column still reaches maxit
+      const double rel = v->slot_bn[q] > 0 ? c->h_res[q] / v->slot_bn[q] : 0.0;
+      const bool conv = rel <= c->opt.rtol;
+      if (!conv && v->slot_its[q] < c->opt.maxit) continue;
+      hz_server::Req& r = v->reqs.at(v->slot[q].req);
+      if (r.u.empty()) r.u.resize((size_t)r.ns * n);
+      col_get(c->X, v->d_col, n, s, q, st);
+      CK(cudaMemcpyAsync(&r.u[(size_t)v->slot[q].idx * n], v->d_col, n * sizeof(double2), cudaMemcpyDeviceToHost,
+                         st));
+      CK(cudaStreamSynchronize(st));  // d_col is reused by the next retired slot
+      r.iterations = std::max(r.iterations, v->slot_its[q]);
+      r.converged &= conv ? 1 : 0;
+      r.maxrel = std::max(r.maxrel, rel);
+      col_zero(c->B, n, s, q, st);
+      col_zero(c->X, n, s, q, st);
+      col_zero(c->R, n, s, q, st);
+      if (--r.remaining == 0 && *ndone < cap) done_ids[(*ndone)++] = v->slot[q].req;
+      v->slot[q].req = -1;
+    }
+    check_launch();
+    CK(cudaStreamSynchronize(st));
+    return HZ_OK;
+  });
+}
+
+extern "C" int hz_server_fetch(hz_server* v, int64_t id, double* u, hz_stats* stats) {
+  if (!v || !u) return fail(HZ_EINVAL, "bad argument");
+  auto it = v->reqs.find(id);
+  if (it == v->reqs.end() || it->second.remaining != 0) return fail(HZ_EINVAL, "request unknown or not finished");
+  hz_server::Req& r = it->second;
+  std::memcpy(u, r.u.data(), r.u.size() * sizeof(double2));
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->iterations = r.iterations;
+    stats->converged = r.converged;
+    stats->ncols = r.ns;
+    stats->max_rel_residual = r.maxrel;
+  }
+  const int rc = r.converged ? HZ_OK : HZ_ENOTCONV;
+  if (rc != HZ_OK) g_last_error = "FGMRES reached maxit before rtol";
+  v->reqs.erase(it);
+  return rc;
+}
+
+extern "C" int hz_server_pending(const hz_server* v, int32_t* queued, int32_t* active) {
+  if (!v || !queued || !active) return fail(HZ_EINVAL, "bad argument");
+  *queued = (int32_t)v->queue.size();
+  int a = 0;
+  for (const auto& q : v->slot) a += q.req >= 0;
+  *active = a;
+  return HZ_OK;
+}
+
+extern "C" void hz_server_free(hz_server* v) { delete v; }
+
+// ---------------------------------------------------------------------------
+// FWI misfit and adjoint-state gradient (hz_receiver_operator, hz_fwi_gradient)
+// ---------------------------------------------------------------------------
+namespace {
+
+struct TmpPool {  // device buffers of one call, released after the stream drains
+  DevPool p;
+  cudaStream_t st;
+  ~TmpPool() {
+    cudaStreamSynchronize(st);
+    p.release();
+  }
+};
+
+void fwi_prepare(hz_ctx* c) {
+  if (c->fwi_ready) return;
+  const Mesh& m = c->fine;
+  const int64_t ne = m.ne;
+  std::vector<int> l2g((size_t)ne * NLOC);
+  std::vector<double> vol(ne), farea((size_t)ne * 4, 0.0);
+  for (int64_t e = 0; e < ne; ++e) {
+    double P[12];
+    for (int a = 0; a < 4; ++a)
+      for (int d = 0; d < 3; ++d) P[3 * a + d] = m.xyz[3 * m.tets[4 * e + a] + d];
+    vol[e] = elem_geom(P).vol;
+    for (int f = 0; f < 4; ++f)
+      if (m.nbr[4 * e + f] < 0 && m.ftag[4 * e + f] == HZ_BC_ROBIN) farea[4 * e + f] = face_area(P, f);
+    for (int i = 0; i < NLOC; ++i) {
+      const int64_t g = c->space.l2g[NLOC * e + i];
+      l2g[NLOC * e + i] = c->space.dirichlet[g] ? -1 : (int)g;
+    }
+  }
+  c->d_fwi_l2g = c->pool.upload(l2g, c->st);
+  c->d_fwi_vol = c->pool.upload(vol, c->st);
+  c->d_fwi_farea = c->pool.upload(farea, c->st);
+  c->d_fwi_m = c->pool.upload(c->mvals, c->st);
+  CK(cudaStreamSynchronize(c->st));
+  c->fwi_ready = true;
+}
+
+void receiver_operator(const hz_ctx* c, const double* rec_xyz, int nr, int32_t* idx, double* w) {
+  std::vector<int64_t> elem(nr);
+  std::vector<double> lam(4 * (size_t)nr);
+  locate_points(c->fine, rec_xyz, nr, elem.data(), lam.data());
+  for (int k = 0; k < nr; ++k) {
+    if (elem[k] < 0) throw HzError{HZ_EINVAL, "receiver outside the mesh"};
+    double phi[NLOC];
+    p3_basis(&lam[4 * (size_t)k], phi);
+    for (int i = 0; i < NLOC; ++i) {
+      const int64_t g = c->space.l2g[NLOC * elem[k] + i];
+      const bool keep = !c->space.dirichlet[g] && phi[i] != 0.0;
+      idx[(size_t)k * NLOC + i] = keep ? (int32_t)g : -1;
+      w[(size_t)k * NLOC + i] = keep ? phi[i] : 0.0;
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" int hz_receiver_operator(const hz_ctx* c, const double* rec_xyz, int32_t nr, int32_t* idx, double* w) {
+  if (!c || nr < 0 || (nr > 0 && (!rec_xyz || !idx || !w))) return fail(HZ_EINVAL, "bad argument");
+  return guarded([&]() -> int {
+    receiver_operator(c, rec_xyz, nr, idx, w);
+    return HZ_OK;
+  });
+}
+
+extern "C" int hz_fwi_gradient(hz_ctx* c, const double* src_xyz, const double* src_amp, int32_t ns,
+                               const double* rec_xyz, int32_t nr, const double* d_obs, double* chi, double* grad,
+                               double* d_syn, hz_stats* stats) {
+  if (!c || !src_xyz || !src_amp || !rec_xyz || !grad || ns < 1 || nr < 1) return fail(HZ_EINVAL, "bad argument");
+  return guarded([&]() -> int {
+    join_user(c);
+    const double t0 = now_s();
+    const int64_t n = c->space.n, ne = c->fine.ne;
+    cudaStream_t st = c->st;
+    // receivers: P as [nr][20] (dof, weight) and its transpose in CSR over the touched dofs
+    std::vector<int> pidx((size_t)nr * NLOC);
+    std::vector<double> pw((size_t)nr * NLOC);
+    receiver_operator(c, rec_xyz, nr, pidx.data(), pw.data());
+    std::map<int, std::vector<std::pair<int, double>>> rows;
+    for (int k = 0; k < nr; ++k)
+      for (int i = 0; i < NLOC; ++i)
+        if (pidx[(size_t)k * NLOC + i] >= 0) rows[pidx[(size_t)k * NLOC + i]].push_back({k, pw[(size_t)k * NLOC + i]});
+    std::vector<int> trow, tptr{0}, tk;
+    std::vector<double> tw;
+    for (auto& kv : rows) {
+      trow.push_back(kv.first);
+      for (auto& e : kv.second) {
+        tk.push_back(e.first);
+        tw.push_back(e.second);
+      }
+      tptr.push_back((int)tk.size());
+    }
+    const int nt = (int)trow.size();
+    fwi_prepare(c);
+    const P3Tables& T = p3_tables();
+    CK(fwi_set_tables(&T.M[0][0], &T.B[0][0][0], st));
+    TmpPool tmp{DevPool(), st};
+    int* d_pidx = tmp.p.upload(pidx, st);
+    double* d_pw = tmp.p.upload(pw, st);
+    int* d_trow = tmp.p.upload(trow, st);
+    int* d_tptr = tmp.p.upload(tptr, st);
+    int* d_tk = tmp.p.upload(tk, st);
+    double* d_tw = tmp.p.upload(tw, st);
+    double* d_g = tmp.p.alloc<double>(ne);
+    double* d_chi = tmp.p.alloc<double>(1);
+    const int bs = std::min<int>(c->opt.max_block, ns);
+    double2* d_r = tmp.p.alloc<double2>((size_t)bs * nr);
+    double2* d_d = tmp.p.alloc<double2>((size_t)bs * nr);
+    double2* d_u = tmp.p.alloc<double2>((size_t)n * bs);
+    CK(cudaMemsetAsync(d_g, 0, ne * sizeof(double), st));
+    CK(cudaMemsetAsync(d_chi, 0, sizeof(double), st));
+    int rc = HZ_OK;
+    hz_stats agg;
+    std::memset(&agg, 0, sizeof(agg));
+    agg.converged = 1;
+    auto add_stats = [&](const hz_stats& a) {
+      agg.iterations = std::max(agg.iterations, a.iterations);
+      agg.restarts += a.restarts;
+      agg.converged &= a.converged;
+      agg.max_rel_residual = std::max(agg.max_rel_residual, a.max_rel_residual);
+    };
+    std::vector<double2> h_r;
+    for (int q0 = 0; q0 < ns; q0 += c->opt.max_block) {
+      const int s = std::min(c->opt.max_block, ns - q0);
+      ensure_workspace(c, s);
+      // forward: A u = F (point sources)
+      std::vector<int> idx;
+      std::vector<double2> val;
+      for (int q = 0; q < s; ++q)
+        point_source_entries(c, &src_xyz[3 * (size_t)(q0 + q)], &src_amp[2 * (size_t)(q0 + q)], s, q, idx, val);
+      int* d_si = tmp.p.upload(idx, st);
+      double2* d_sv = tmp.p.upload(val, st);
+      axpy_cols_zero(c->B, n * s, st);
+      scatter_point_sources(c->B, n, s, d_si, d_sv, (int)idx.size(), st);
+      hz_stats a;
+      int r = fgmres(c, s, &a);
+      check_launch();
+      if (r != HZ_OK) rc = r;
+      add_stats(a);
+      CK(cudaMemcpyAsync(d_u, c->X, (size_t)n * s * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+      // residual at the receivers and misfit
+      if (d_obs)
+        CK(cudaMemcpyAsync(d_d, d_obs + 2 * (size_t)q0 * nr, (size_t)s * nr * sizeof(double2),
+                           cudaMemcpyHostToDevice, st));
+      fwi_residual(nr, s, d_pidx, d_pw, d_u, d_obs ? d_d : nullptr, d_r, st);
+      fwi_chi((int64_t)s * nr, d_r, d_chi, st);
+      if (d_syn) {
+        h_r.resize((size_t)s * nr);
+        CK(cudaMemcpyAsync(h_r.data(), d_r, h_r.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (size_t i = 0; i < h_r.size(); ++i) {
+          const double* dd = d_obs ? d_obs + 2 * ((size_t)q0 * nr + i) : nullptr;
+          d_syn[2 * ((size_t)q0 * nr + i)] = h_r[i].x + (dd ? dd[0] : 0.0);
+          d_syn[2 * ((size_t)q0 * nr + i) + 1] = h_r[i].y + (dd ? dd[1] : 0.0);
+        }
+      }
+      // adjoint: A lambda = P^T conj(r)
+      axpy_cols_zero(c->B, n * s, st);
+      fwi_adjoint_rhs(nt, s, nr, d_trow, d_tptr, d_tk, d_tw, d_r, c->B, st);
+      r = fgmres(c, s, &a);
+      check_launch();
+      if (r != HZ_OK) rc = r;
+      add_stats(a);
+      // g_e -= Re sum_s lambda_e^T dA/dm_e u_e
+      fwi_gradient(ne, s, c->d_fwi_l2g, c->d_fwi_vol, c->d_fwi_farea, c->d_fwi_m, c->omega, d_u, c->X, d_g, st);
+      check_launch();
+    }
+    CK(cudaMemcpyAsync(grad, d_g, ne * sizeof(double), cudaMemcpyDeviceToHost, st));
+    double h_chi = 0;
+    CK(cudaMemcpyAsync(&h_chi, d_chi, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (chi) *chi = h_chi;
+    agg.ncols = 2 * ns;
+    agg.solve_seconds = now_s() - t0;
+    agg.setup_seconds = c->setup_s;
+    agg.factor_seconds = c->factor_s;
+    if (stats) *stats = agg;
+    if (rc != HZ_OK) g_last_error = "FGMRES reached maxit before rtol";
+    return rc;
+  });
+}

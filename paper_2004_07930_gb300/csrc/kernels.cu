@@ -153,6 +153,30 @@ void axpy_cols_zero(double2* X, int64_t count, cudaStream_t st) {
   if (count) { k_zero<<<grid_for(count, 256), 256, 0, st>>>(X, count); count_launch(); }
 }
 
+// one column c of an [n][s] block: zero it, copy it to another block, or
+// extract it as a contiguous vector
+__global__ void k_col_zero(double2* X, int64_t n, int s, int c) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) X[i * s + c] = make_double2(0.0, 0.0);
+}
+__global__ void k_col_copy(const double2* __restrict__ X, double2* __restrict__ Y, int64_t n, int s, int c) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) Y[i * s + c] = X[i * s + c];
+}
+__global__ void k_col_get(const double2* __restrict__ X, double2* __restrict__ y, int64_t n, int s, int c) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = X[i * s + c];
+}
+void col_zero(double2* X, int64_t n, int s, int c, cudaStream_t st) {
+  if (n) { k_col_zero<<<grid_for(n, 256), 256, 0, st>>>(X, n, s, c); count_launch(); }
+}
+void col_copy(const double2* X, double2* Y, int64_t n, int s, int c, cudaStream_t st) {
+  if (n) { k_col_copy<<<grid_for(n, 256), 256, 0, st>>>(X, Y, n, s, c); count_launch(); }
+}
+void col_get(const double2* X, double2* y, int64_t n, int s, int c, cudaStream_t st) {
+  if (n) { k_col_get<<<grid_for(n, 256), 256, 0, st>>>(X, y, n, s, c); count_launch(); }
+}
+
 // ---------------------------------------------------------------------------
 // Right-hand sides (K11) and layout changes
 // ---------------------------------------------------------------------------

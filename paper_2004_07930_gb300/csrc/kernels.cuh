@@ -147,5 +147,18 @@ void scatter_point_sources(double2* B, int64_t n, int s, const int* idx, const d
 void transpose_to_rows(const double2* F, double2* B, int64_t n, int s, cudaStream_t st);    // [s][n] -> [n][s]
 void transpose_from_rows(const double2* B, double2* F, int64_t n, int s, cudaStream_t st);  // [n][s] -> [s][n]
 void cast_copy(const double2* X, double2* Y, int64_t count, cudaStream_t st);
+// one column c of an [n][s] block
+void col_zero(double2* X, int64_t n, int s, int c, cudaStream_t st);
+void col_copy(const double2* X, double2* Y, int64_t n, int s, int c, cudaStream_t st);
+void col_get(const double2* X, double2* y, int64_t n, int s, int c, cudaStream_t st);  // y [n]
+// FWI misfit / adjoint / gradient (fwi.cu); blocks node-major [n][s]
+cudaError_t fwi_set_tables(const double* Mhat, const double* Bhat, cudaStream_t st);  // Mhat [20][20], Bhat [4][20][20]
+void fwi_residual(int nr, int s, const int* pidx, const double* pw, const double2* U, const double2* d, double2* r,
+                  cudaStream_t st);
+void fwi_chi(int64_t m, const double2* r, double* chi, cudaStream_t st);
+void fwi_adjoint_rhs(int nt, int s, int nr, const int* trow, const int* tptr, const int* tk, const double* tw,
+                     const double2* r, double2* B, cudaStream_t st);
+void fwi_gradient(int64_t ne, int s, const int* l2g, const double* vol, const double* farea, const double* m,
+                  double omega, const double2* U, const double2* L, double* g, cudaStream_t st);
 
 }  // namespace hz

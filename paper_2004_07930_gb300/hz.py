@@ -19,7 +19,9 @@ HZ_PREC_FP64, HZ_PREC_MIXED = 0, 1
 
 EXPORTS = ["hz_default_options", "hz_setup", "hz_ndof", "hz_dof_coords", "hz_get_info", "hz_solve",
            "hz_solve_rhs", "hz_apply_A", "hz_apply_prec", "hz_matrix_csr", "hz_free", "hz_strerror",
-           "hz_last_error", "hz_profile_begin", "hz_profile_end", "hz_apply_A_noalloc"]
+           "hz_last_error", "hz_profile_begin", "hz_profile_end", "hz_apply_A_noalloc", "hz_server_create",
+           "hz_server_submit", "hz_server_step", "hz_server_fetch", "hz_server_pending", "hz_server_free",
+           "hz_receiver_operator", "hz_fwi_gradient"]
 HZ_NOALLOC_MAX_ENTRIES = 1048576  # complex entries per work block of hz_apply_A_noalloc (n * s)
 
 
@@ -90,6 +92,15 @@ def load():
     lib.hz_apply_prec.argtypes = [P, P, P, C.c_int32, C.c_int32]
     lib.hz_matrix_csr.argtypes = [P, P, P, P]
     lib.hz_apply_A_noalloc.argtypes = [P, P, P, C.c_int32, P]
+    lib.hz_server_create.argtypes = [P, C.c_int32, C.POINTER(P)]
+    lib.hz_server_submit.argtypes = [P, C.c_int64, P, P, C.c_int32]
+    lib.hz_server_step.argtypes = [P, P, C.c_int32, C.POINTER(C.c_int32)]
+    lib.hz_server_fetch.argtypes = [P, C.c_int64, P, C.POINTER(HzStats)]
+    lib.hz_server_pending.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    lib.hz_server_free.argtypes = [P]
+    lib.hz_server_free.restype = None
+    lib.hz_receiver_operator.argtypes = [P, P, C.c_int32, P, P]
+    lib.hz_fwi_gradient.argtypes = [P, P, P, C.c_int32, P, C.c_int32, P, P, P, P, C.POINTER(HzStats)]
     lib.hz_profile_begin.argtypes = [P]
     lib.hz_profile_end.argtypes = [P, C.POINTER(HzPhaseTime), C.c_int32, C.POINTER(C.c_int32)]
     lib.hz_free.argtypes = [P]
@@ -167,6 +178,7 @@ class Solver:
         n = C.c_int64()
         _check(lib.hz_ndof(ctx, C.byref(n)))
         self.n = n.value
+        self.ne = len(vel)
 
     @classmethod
     def from_problem(cls, prob, options=None, stream=None, **kw):
@@ -271,3 +283,85 @@ class Solver:
         if rc != HZ_ENOTCONV or raise_on_notconv:
             _check(rc)
         return U, st.asdict()
+
+    def receiver_operator(self, rec_xyz):
+        """(idx [nr, 20] int32, w [nr, 20]): receiver k samples
+        sum_i w[k, i] u[idx[k, i]] (idx -1: no entry)."""
+        rec = np.ascontiguousarray(rec_xyz, dtype=np.float64).reshape(-1, 3)
+        idx = np.empty((len(rec), 20), dtype=np.int32)
+        w = np.empty((len(rec), 20), dtype=np.float64)
+        _check(self._lib.hz_receiver_operator(self._ctx, rec.ctypes.data, len(rec), idx.ctypes.data, w.ctypes.data))
+        return idx, w
+
+    def fwi_gradient(self, src_xyz, rec_xyz, d_obs=None, src_amp=None, raise_on_notconv=True):
+        """(chi, grad [ne], d_syn [ns, nr], stats): least-squares misfit of
+        the receiver data and its gradient with respect to the per-element
+        squared slowness (adjoint state, on the device)."""
+        src = np.ascontiguousarray(src_xyz, dtype=np.float64).reshape(-1, 3)
+        rec = np.ascontiguousarray(rec_xyz, dtype=np.float64).reshape(-1, 3)
+        ns, nr = len(src), len(rec)
+        amp = np.ones(ns, dtype=np.complex128) if src_amp is None else \
+            np.ascontiguousarray(src_amp, dtype=np.complex128).reshape(-1)
+        dp = None
+        if d_obs is not None:
+            d_obs = np.ascontiguousarray(d_obs, dtype=np.complex128).reshape(ns, nr)
+            dp = d_obs.ctypes.data
+        chi = C.c_double()
+        grad = np.empty(self.ne, dtype=np.float64)
+        dsyn = np.empty((ns, nr), dtype=np.complex128)
+        st = HzStats()
+        rc = self._lib.hz_fwi_gradient(self._ctx, src.ctypes.data, amp.ctypes.data, ns, rec.ctypes.data, nr, dp,
+                                       C.byref(chi), grad.ctypes.data, dsyn.ctypes.data, C.byref(st))
+        if rc != HZ_ENOTCONV or raise_on_notconv:
+            _check(rc)
+        return chi.value, grad, dsyn, st.asdict()
+
+
+class Server:
+    """Continuous-batching request loop on one Solver (mesh + frequency):
+    `slots` right-hand-side columns shared by the queued requests."""
+
+    def __init__(self, solver, slots):
+        self.solver = solver
+        self._lib = solver._lib
+        h = C.c_void_p()
+        _check(self._lib.hz_server_create(solver._ctx, int(slots), C.byref(h)))
+        self._h = h
+        self.slots = slots
+
+    def submit(self, request_id, src_xyz, src_amp=None):
+        src = np.ascontiguousarray(src_xyz, dtype=np.float64).reshape(-1, 3)
+        amp = np.ones(len(src), dtype=np.complex128) if src_amp is None else \
+            np.ascontiguousarray(src_amp, dtype=np.complex128).reshape(-1)
+        _check(self._lib.hz_server_submit(self._h, int(request_id), src.ctypes.data, amp.ctypes.data, len(src)))
+
+    def step(self):
+        """One restart cycle; returns the ids of the requests that finished."""
+        done = np.empty(4096, dtype=np.int64)
+        nd = C.c_int32()
+        _check(self._lib.hz_server_step(self._h, done.ctypes.data, len(done), C.byref(nd)))
+        return done[: nd.value].tolist()
+
+    def fetch(self, request_id, ns):
+        u = np.empty((ns, self.solver.n), dtype=np.complex128)
+        st = HzStats()
+        rc = self._lib.hz_server_fetch(self._h, int(request_id), u.ctypes.data, C.byref(st))
+        if rc not in (HZ_OK, HZ_ENOTCONV):
+            _check(rc)
+        return u, st.asdict()
+
+    def pending(self):
+        q, a = C.c_int32(), C.c_int32()
+        _check(self._lib.hz_server_pending(self._h, C.byref(q), C.byref(a)))
+        return q.value, a.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.hz_server_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

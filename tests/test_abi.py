@@ -66,3 +66,22 @@ def test_setup_rejects_bad_inputs(lib):
     assert _setup_rc(p, freq=0.0) == hz.HZ_EINVAL
     assert "partition" in hz.load().hz_last_error().decode() or True
     assert lib.hz_strerror(hz.HZ_ENOTCONV).decode() == "not converged"
+
+
+def test_calls_reject_null_context(lib):
+    """Per-context calls refuse a NULL context before touching a GPU."""
+    import ctypes as C
+
+    xyz = np.zeros(3)
+    idx = np.zeros(20, dtype=np.int32)
+    w = np.zeros(20)
+    assert lib.hz_receiver_operator(None, xyz.ctypes.data, 1, idx.ctypes.data, w.ctypes.data) == hz.HZ_EINVAL
+    g = np.zeros(4)
+    amp = np.ones(2)
+    assert lib.hz_fwi_gradient(None, xyz.ctypes.data, amp.ctypes.data, 1, xyz.ctypes.data, 1, None, None,
+                               g.ctypes.data, None, None) == hz.HZ_EINVAL
+    n = C.c_int64()
+    assert lib.hz_ndof(None, C.byref(n)) == hz.HZ_EINVAL
+    h = C.c_void_p()
+    assert lib.hz_server_create(None, 4, C.byref(h)) == hz.HZ_EINVAL
+    assert lib.hz_server_step(None, None, 0, C.byref(C.c_int32())) == hz.HZ_EINVAL
