@@ -110,7 +110,7 @@ def test_gradient_directional_fd_full_size():
     assert st["converged"] == 1 and chi > 0
     rng = np.random.Generator(np.random.PCG64(2))
     dm = m0 * np.sign(g) * rng.uniform(0.5, 1.5, len(m0))
-    h = 1e-3
+    h = 1e-4  # the +-h dm models change chi by ~35%: central differences still O(h^2) accurate
     cp = fwi.misfit_and_gradient(p, m0 + h * dm, src, rec, d_obs, options=opt)[0]
     cm = fwi.misfit_and_gradient(p, m0 - h * dm, src, rec, d_obs, options=opt)[0]
     fd = (cp - cm) / (2 * h)

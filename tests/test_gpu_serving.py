@@ -40,7 +40,7 @@ def _oracle_wavefields(p, S, src):
 def test_request_same_alone_and_in_mix(precision):
     torch_cuda()
     p = wl.cube_problem(ncell=4, nparts_xyz=(2, 2, 1))
-    with hz.Solver.from_problem(p, rtol=1e-8, precision=precision, restart=8) as S:
+    with hz.Solver.from_problem(p, rtol=1e-8, precision=precision, restart=3) as S:
         alone = hz.Server(S, 4)
         alone.submit(7, SRC_A)
         uA, stA = _drain(alone, {7: 2})[7]
