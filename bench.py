@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--maxit", type=int, default=500, help="FGMRES iteration cap (lower it only for profiling runs)")
     ap.add_argument("--coarse", choices=["gmres", "none", "direct"], default="gmres",
                     help="coarse level of the headline forms (the paper's: gmres, 10 inner steps)")
+    ap.add_argument("--spmm-sweep", action="store_true",
+                    help="instead of the throughput line: HBM and FP64 rates of the product with A "
+                         "(hz_apply_A, device blocks) for block widths 1..16 on the bench workload")
     ap.add_argument("--serving", action="store_true",
                     help="instead of the throughput line: a seeded Poisson stream of point-source requests over "
                          "several frequencies through the continuous-batching server (p50/p99 latency, RHS/s)")
@@ -293,6 +296,41 @@ def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, **o
 MAXIT = 500
 
 
+def run_spmm_sweep(args):
+    """k_spmm_split alone: for s = 1, 2, 4, 8, 16 the product Y = A X through
+    hz_apply_A on device blocks, timed by the library's CUDA events around
+    the product only (the layout transposes of hz_apply_A are outside the
+    recorded phase). Algorithmic bytes: 12 per nonzero (value + column),
+    row pointers, X and Y once; flops: 4 per nonzero and column."""
+    import torch
+
+    from paper_2004_07930_gb300 import hz
+
+    torch.cuda.set_device(0)
+    hz.load()
+    prob, desc = problem(args.config)
+    hbm, peak_kind, _ = peaks()
+    out = {}
+    with hz.Solver.from_problem(prob, precision=hz.HZ_PREC_FP64, coarse_mode=hz.HZ_COARSE_NONE) as S:
+        for s in (1, 2, 4, 8, 16):
+            X = torch.randn((s, S.n), dtype=torch.complex128, device="cuda")
+            for _ in range(3):
+                S.apply_A(X)
+            torch.cuda.synchronize()
+            S.profile_begin()
+            for _ in range(20):
+                S.apply_A(X)
+            ph = S.profile_end()["spmm_A"]
+            sec = ph["ms"] / 1e3
+            out[s] = {"calls": ph["calls"], "us_per_call": 1e6 * sec / ph["calls"],
+                      "gbs": ph["bytes"] / sec / 1e9, "hbm_frac": ph["bytes"] / sec / 1e9 / hbm,
+                      "fp64_gflops": ph["flops"] / sec / 1e9,
+                      "fp64_frac": ph["flops"] / sec / 1e9 / FP64_NOMINAL_GFLOPS}
+    print(json.dumps({"mode": "spmm_sweep", "kernel": "k_spmm_split", "config": {"workload": desc},
+                      "hbm_peak_gbs": hbm, "hbm_peak_kind": peak_kind, "fp64_peak_gflops": FP64_NOMINAL_GFLOPS,
+                      "by_block_width": out}), flush=True)
+
+
 def run_serving(args):
     """Continuous batching of a seeded Poisson request stream: every request
     carries 1-32 point sources at uniform surface positions (z = 100 m) and
@@ -361,6 +399,9 @@ def main():
         return
     if args.serving:
         run_serving(args)
+        return
+    if args.spmm_sweep:
+        run_spmm_sweep(args)
         return
     ws, rank, local = dist_env()
     import torch
