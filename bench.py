@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--maxit", type=int, default=500, help="FGMRES iteration cap (lower it only for profiling runs)")
     ap.add_argument("--coarse", choices=["gmres", "none", "direct"], default="gmres",
                     help="coarse level of the headline forms (the paper's: gmres, 10 inner steps)")
+    ap.add_argument("--tensor-cores", type=int, choices=[-1, 0, 1], default=-1,
+                    help="mixed form: front sweeps on the tcgen05 tensor cores (1) or SIMT (0); -1: library default")
     ap.add_argument("--spmm-sweep", action="store_true",
                     help="instead of the throughput line: HBM and FP64 rates of the product with A "
                          "(hz_apply_A, device blocks) for block widths 1..16 on the bench workload")
@@ -241,6 +243,8 @@ def run_reference(args):
 
 def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, **opts):
     prec = hz.HZ_PREC_MIXED if form == "mixed" else hz.HZ_PREC_FP64
+    if TENSOR_CORES >= 0:
+        opts["tensor_cores"] = TENSOR_CORES
     t0 = time.time()
     S = hz.Solver.from_problem(prob, precision=prec, rtol=1e-6, stream=stream, maxit=MAXIT, **opts)
     setup_wall = time.time() - t0
@@ -294,6 +298,7 @@ def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, **o
 
 
 MAXIT = 500
+TENSOR_CORES = -1
 
 
 def run_spmm_sweep(args):
@@ -391,9 +396,10 @@ def run_serving(args):
 
 
 def main():
-    global MAXIT
+    global MAXIT, TENSOR_CORES
     args = parse()
     MAXIT = args.maxit
+    TENSOR_CORES = args.tensor_cores
     if args.impl == "reference":
         run_reference(args)
         return
@@ -440,7 +446,17 @@ def main():
     ph = r["phases"]["fronts"]
     per_app = ph["bytes"] / ph["calls"]  # algorithmic bytes of one application of the fine local solves
     hbm_achieved = ph["bytes"] / (ph["ms"] / 1e3) / 1e9
-    if head == "mixed":
+    tc_on = (TENSOR_CORES if TENSOR_CORES >= 0 else hz.default_options().tensor_cores) == 1
+    if head == "mixed" and tc_on:
+        # tcgen05 sweeps: the tensor rate is far above what 8 bytes per factor entry can feed,
+        # so the roof is HBM; the DRAM traffic of these kernels has not been captured with ncu
+        roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm, "unit": "GB/s", "frac": hbm_achieved / hbm,
+                "traffic": None, "traffic_unit": "bytes per application of the fine local solves",
+                "kernel": "fine local solves (k_mf_tile_tc on tcgen05 + k_mf_tile for small tiles + k_mf_reduce, "
+                          "TF32 factors, FP32 accumulation)",
+                "peak_kind": peak_kind, "algorithmic_bytes_per_application": per_app,
+                "fp32_tflops_achieved": ph["flops"] / (ph["ms"] / 1e3) / 1e12, "launches": ph["calls"]}
+    elif head == "mixed":
         # s = 16 puts the FP32 sweeps above the SIMT FP32 ridge (16 flops per factor byte), so the
         # binding roof is the FP32 FMA rate; the HBM figures are reported beside it
         achieved = ph["flops"] / (ph["ms"] / 1e3) / 1e12
@@ -463,7 +479,8 @@ def main():
         "metric": "RHS solved/s at rtol 1e-6", "value": r["rhs_per_s"], "unit": "RHS/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "c64 fronts + c128 Krylov/SpMM/coarse" if head == "mixed" else "c128",
+        "dtype": ("tf32 x fp32 tensor-core fronts" if tc_on else "c64 fronts") + " + c128 Krylov/SpMM/coarse"
+                 if head == "mixed" else "c128",
         "data": "synthetic (seeded Overthrust-like model; no real data)",
         "config": {"workload": desc, "n": r["info"]["n"], "nnz": r["info"]["nnz"], "sources_per_step": 16,
                    "rtol": 1e-6, "l2_flush": "inputs larger than L2 (factors %.1f GB)" %

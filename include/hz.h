@@ -90,6 +90,9 @@ typedef struct hz_options {
   int32_t verbose;          /* 0 silent */
   int32_t use_graphs;       /* 1 (default): replay the local-solve and coarse-solve launch sequences
                                as captured CUDA graphs; 0: launch them one by one */
+  int32_t tensor_cores;     /* mixed form only. 1: front-sweep tiles of at least 32 rows and 32 reduction
+                               indices run on the tcgen05 tensor cores (factors rounded to TF32, FP32
+                               accumulation) for blocks of 9-64 columns; 0 (default): SIMT FP32 sweeps */
 } hz_options;
 
 typedef struct hz_stats {

@@ -87,6 +87,7 @@ struct MFHost {
   int64_t factor_entries = 0, front_entries = 0, stored_entries = 0;
   int max_front = 0, nfronts = 0, nlevels = 0;
   std::vector<int> level_ptr, ftile_ptr, btile_ptr, frb_ptr, brb_ptr;
+  std::vector<int> fs_ptr, bs_ptr, ftc_ptr, btc_ptr;  // tensor-core mode split of the tile lists
   std::vector<int64_t> level_row;
   // per-level algorithmic work of one solve sweep (complex multiply-adds per column)
   std::vector<double> fwd_cmacs, bwd_cmacs;
@@ -98,8 +99,9 @@ constexpr int MF_TILE_ROWS = 128;  // output rows per sweep tile (MF_TILE in mf.
 constexpr int MF_TILE_K = 128;     // reduction length per sweep tile (MF_TK in mf.cu)
 
 void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const FrontTree*>& trees,
-              const std::vector<int64_t>& sub_off, bool fp32, DevMF& mf, MFHost& info, DevPool& pool,
+              const std::vector<int64_t>& sub_off, bool fp32, bool tc, DevMF& mf, MFHost& info, DevPool& pool,
               cudaStream_t st) {
+  tc = tc && fp32;
   const size_t ns = mats.size();
   std::vector<int> base(ns + 1, 0);
   for (size_t i = 0; i < ns; ++i) base[i + 1] = base[i] + (int)trees[i]->k.size();
@@ -239,6 +241,30 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
   info.btile_ptr.assign(1, 0);
   info.frb_ptr.assign(1, 0);
   info.brb_ptr.assign(1, 0);
+  // tensor-core mode: eligible tiles go to the tcgen05 kernel with their factor
+  // block packed (TF32 planes, K-major core matrices), the rest to the SIMT kernel
+  std::vector<int4> fs, bsl, ftc, btc;
+  std::vector<int64_t> ftc_off, btc_off;
+  int64_t tc_bytes = 0;
+  info.fs_ptr.assign(1, 0);
+  info.bs_ptr.assign(1, 0);
+  info.ftc_ptr.assign(1, 0);
+  info.btc_ptr.assign(1, 0);
+  auto classify = [&](bool fwd, const int4& tile) {
+    const int g = tile.x, r0 = tile.y, c0 = tile.z;
+    const int nout = fwd ? f[g] : k[g];
+    const int kend = fwd ? (r0 < k[g] ? std::min(k[g], r0 + MF_TILE_ROWS) : k[g]) : f[g];
+    const int kbeg = fwd ? c0 : std::max(c0, r0);
+    const int kstop = std::min(kend, c0 + MF_TILE_K);
+    const int nr = std::min(MF_TILE_ROWS, nout - r0), nk = kstop - kbeg;
+    if (tc && nr >= TC_MIN_ROWS && nk >= TC_MIN_K) {
+      (fwd ? ftc : btc).push_back(tile);
+      (fwd ? ftc_off : btc_off).push_back(tc_bytes);
+      tc_bytes += tc_tile_bytes(nr, nk);
+    } else {
+      (fwd ? fs : bsl).push_back(tile);
+    }
+  };
   info.fwd_cmacs.assign(maxh + 1, 0.0);
   info.bwd_cmacs.assign(maxh + 1, 0.0);
   int64_t max_slots = 1;
@@ -253,19 +279,27 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
         const int nk = (kend + MF_TILE_K - 1) / MF_TILE_K;
         if (nk == 1) {
           ftiles.push_back(make_int4(g, r0, 0, -1));
+          classify(true, ftiles.back());
           continue;
         }
         frb.push_back(make_int4(g, r0, nk, fslot));
-        for (int c0 = 0; c0 < kend; c0 += MF_TILE_K) ftiles.push_back(make_int4(g, r0, c0, fslot++));
+        for (int c0 = 0; c0 < kend; c0 += MF_TILE_K) {
+          ftiles.push_back(make_int4(g, r0, c0, fslot++));
+          classify(true, ftiles.back());
+        }
       }
       for (int j0 = 0; j0 < k[g]; j0 += MF_TILE_ROWS) {
         const int nk = (f[g] - j0 + MF_TILE_K - 1) / MF_TILE_K;
         if (nk == 1) {
           btiles.push_back(make_int4(g, j0, j0, -1));
+          classify(false, btiles.back());
           continue;
         }
         brb.push_back(make_int4(g, j0, nk, bslot));
-        for (int c0 = j0; c0 < f[g]; c0 += MF_TILE_K) btiles.push_back(make_int4(g, j0, c0, bslot++));
+        for (int c0 = j0; c0 < f[g]; c0 += MF_TILE_K) {
+          btiles.push_back(make_int4(g, j0, c0, bslot++));
+          classify(false, btiles.back());
+        }
       }
       const double kk = k[g], mm = f[g] - k[g];
       info.fwd_cmacs[l] += kk * (kk + 1) / 2 + kk * mm;
@@ -276,6 +310,10 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
     info.btile_ptr.push_back((int)btiles.size());
     info.frb_ptr.push_back((int)frb.size());
     info.brb_ptr.push_back((int)brb.size());
+    info.fs_ptr.push_back((int)fs.size());
+    info.bs_ptr.push_back((int)bsl.size());
+    info.ftc_ptr.push_back((int)ftc.size());
+    info.btc_ptr.push_back((int)btc.size());
   }
   info.level_row.assign(maxh + 2, 0);
   for (int l = 0; l <= maxh; ++l) {
@@ -329,6 +367,25 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
   mf.F = pool.alloc<double2>(Foff[nf]);
   mf.perturbed = pool.alloc<int>(1);
   CK(cudaMemsetAsync(mf.perturbed, 0, sizeof(int), st));
+  mf.tc = tc ? 1 : 0;
+  if (tc) {
+    mf.fs_ptr_h = info.fs_ptr.data();
+    mf.bs_ptr_h = info.bs_ptr.data();
+    mf.ftc_ptr_h = info.ftc_ptr.data();
+    mf.btc_ptr_h = info.btc_ptr.data();
+    mf.ftiles_s = pool.upload(fs, st);
+    mf.btiles_s = pool.upload(bsl, st);
+    mf.ftiles_tc = pool.upload(ftc, st);
+    mf.btiles_tc = pool.upload(btc, st);
+    mf.ftc_off = pool.upload(ftc_off, st);
+    mf.btc_off = pool.upload(btc_off, st);
+    mf.ftc_n = (int64_t)ftc.size();
+    mf.btc_n = (int64_t)btc.size();
+    mf.tc_bytes = tc_bytes;
+    mf.TC = pool.alloc<unsigned char>((size_t)std::max<int64_t>(tc_bytes, 16));
+    mf.tc_err = pool.alloc<int>(1);
+    CK(cudaMemsetAsync(mf.tc_err, 0, sizeof(int), st));
+  }
 }
 
 void upload_split(const CsrC& A, DevSplitCsr& D, DevPool& pool, cudaStream_t st, bool with_f32 = false) {
@@ -377,7 +434,7 @@ struct LevelDev {             // one level of ORAS on the device
   double amax = 0.0;
 };
 
-void build_level(const Space& sp, const std::vector<Subdomain>& subs, int leaf, bool fp32, LevelDev& L,
+void build_level(const Space& sp, const std::vector<Subdomain>& subs, int leaf, bool fp32, bool tc, LevelDev& L,
                  DevPool& pool, cudaStream_t st) {
   const size_t np = subs.size();
   std::vector<int64_t> sub_off(np + 1, 0);
@@ -400,7 +457,7 @@ void build_level(const Space& sp, const std::vector<Subdomain>& subs, int leaf, 
     tr[i] = &L.trees[i];
     for (const cplx& v : subs[i].A.val) L.amax = std::max(L.amax, std::abs(v));
   }
-  build_mf(mats, tr, sub_off, fp32, L.mf, L.info, pool, st);
+  build_mf(mats, tr, sub_off, fp32, tc, L.mf, L.info, pool, st);
   std::vector<int> gidx(sub_off[np]), own(sp.n, -1);
   for (size_t i = 0; i < np; ++i)
     for (size_t l = 0; l < subs[i].dofs.size(); ++l) {
@@ -415,14 +472,14 @@ void build_level(const Space& sp, const std::vector<Subdomain>& subs, int leaf, 
 }
 
 // A single "subdomain" covering the whole matrix: direct factorisation.
-void build_direct(const Space& sp, const CsrC& A, int leaf, bool fp32, LevelDev& L, DevPool& pool,
+void build_direct(const Space& sp, const CsrC& A, int leaf, bool fp32, bool tc, LevelDev& L, DevPool& pool,
                   cudaStream_t st) {
   std::vector<Subdomain> one(1);
   one[0].dofs.resize(sp.n);
   std::iota(one[0].dofs.begin(), one[0].dofs.end(), 0);
   one[0].owned.assign(sp.n, 1);
   one[0].A = A;
-  build_level(sp, one, leaf, fp32, L, pool, st);
+  build_level(sp, one, leaf, fp32, tc, L, pool, st);
 }
 
 void mesh_from_abi(const hz_mesh* in, Mesh& m) {
@@ -859,6 +916,12 @@ int fgmres(hz_ctx* c, int s, hz_stats* stats) {
     if (all_conv || its >= c->opt.maxit) break;
     ++restarts;
   }
+  for (DevMF* mf : {&c->lf.mf, &c->lc.mf})
+    if (mf->tc_err) {  // a tensor-core tile gave up waiting on one of its barriers
+      int e = 0;
+      CK(cudaMemcpy(&e, mf->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+      if (e) throw HzError{HZ_EINTERNAL, "tensor-core sweep tile timed out on a barrier"};
+    }
   if (stats) {
     stats->iterations = its;
     stats->restarts = restarts;
@@ -926,6 +989,7 @@ int hz_default_options(hz_options* o) {
   o->pivot_tau = 1e-12;
   o->verbose = 0;
   o->use_graphs = 1;
+  o->tensor_cores = 0;
   return HZ_OK;
 }
 
@@ -978,7 +1042,8 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
     const bool mixed = o.precision == HZ_PREC_MIXED;
     upload_split(c->A_host, c->A, c->pool, c->st, mixed);
     std::vector<Subdomain> subs = build_subdomains(c->fine, c->space, part, nparts, mvals, omega);
-    build_level(c->space, subs, o.leaf_size, mixed, c->lf, c->pool, c->st);
+    const bool tc = mixed && o.tensor_cores != 0;
+    build_level(c->space, subs, o.leaf_size, mixed, tc, c->lf, c->pool, c->st);
     subs.clear();
     if (o.coarse_mode != HZ_COARSE_NONE) {
       c->has_coarse = true;
@@ -990,9 +1055,9 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
       upload_real(C.ZT, c->ZT, c->pool, c->st, mixed);
       if (o.coarse_mode == HZ_COARSE_GMRES) {
         std::vector<Subdomain> csubs = build_subdomains(c->coarse, c->cspace, C.part, nparts, C.mvals, omega);
-        build_level(c->cspace, csubs, o.leaf_size, mixed, c->lc, c->pool, c->st);
+        build_level(c->cspace, csubs, o.leaf_size, mixed, tc, c->lc, c->pool, c->st);
       } else {
-        build_direct(c->cspace, C.E, o.leaf_size, mixed, c->lc, c->pool, c->st);
+        build_direct(c->cspace, C.E, o.leaf_size, mixed, tc, c->lc, c->pool, c->st);
       }
     }
     CK(cudaStreamSynchronize(c->st));

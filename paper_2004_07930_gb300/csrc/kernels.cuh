@@ -75,7 +75,33 @@ struct DevMF {
   int* gidx = nullptr;          // [nsub_rows] global row of each sub-vector row (R_i)
   int* own = nullptr;           // [n] sub-vector row of the owning copy (D_i Boolean)
   int* perturbed = nullptr;     // device counter
+  // tensor-core sweeps (complex FP32 form): tiles with at least TC_MIN_ROWS output rows and
+  // TC_MIN_K reduction indices run as tcgen05 MMAs (TF32 inputs, FP32 accumulation in TMEM)
+  // when the block has 16, 32 or 64 columns; the others keep the SIMT kernel
+  int tc = 0;                   // packed tensor-core tiles present
+  int* fs_ptr_h = nullptr;      // host [nlevels+1] forward SIMT tiles per level (tensor-core mode)
+  int* bs_ptr_h = nullptr;      // host [nlevels+1] backward SIMT tiles per level
+  int* ftc_ptr_h = nullptr;     // host [nlevels+1] forward tensor-core tiles per level
+  int* btc_ptr_h = nullptr;     // host [nlevels+1] backward tensor-core tiles per level
+  int4* ftiles_s = nullptr;     // forward tiles left to the SIMT kernel
+  int4* btiles_s = nullptr;
+  int4* ftiles_tc = nullptr;    // forward tensor-core tiles
+  int4* btiles_tc = nullptr;
+  int64_t* ftc_off = nullptr;   // byte offset of each tensor-core tile in TC
+  int64_t* btc_off = nullptr;
+  int64_t ftc_n = 0, btc_n = 0; // tensor-core tiles in each sweep
+  unsigned char* TC = nullptr;  // packed factor tiles (per 16-column chunk: Re plane, Im plane)
+  int64_t tc_bytes = 0;
+  int* tc_err = nullptr;        // device flag: a tensor-core tile gave up waiting on a barrier
 };
+
+// tensor-core tile eligibility (output rows, reduction length) and packing geometry
+constexpr int TC_MIN_ROWS = 32;
+constexpr int TC_MIN_K = 32;
+inline int64_t tc_tile_bytes(int nr, int nk) {  // nr output rows, nk reduction indices
+  const int64_t nr8 = (nr + 7) / 8 * 8, nch = (nk + 15) / 16;
+  return nch * 2 * nr8 * 64;
+}
 
 // --- sparse products ---
 // Y = A X (mode 0) or Y = B - A X (mode 1); X, Y, B row-major [n][s] complex
@@ -92,7 +118,8 @@ void scatter_owned(const int* own, int64_t n, const double2* Xsub, const double2
 
 // --- multifrontal ---
 void mf_factor(DevMF& mf, double tau_abs, cudaStream_t st);
-void mf_solve(DevMF& mf, void* Xsub, int s, cudaStream_t st);   // Xsub double2 or float2 (mf.fp32)
+void mf_solve(DevMF& mf, void* Xsub, int s, cudaStream_t st);  // Xsub double2 or float2 (mf.fp32)
+bool mf_tc_usable(const DevMF& mf, int s);  // the block width runs the tensor-core sweeps
 void gather_rows_f32(const int* idx, int64_t nrows, const double2* X, float2* Y, int s, cudaStream_t st);
 void scatter_owned_f32(const int* own, int64_t n, const float2* Xsub, const double2* Q, double2* Z, int s,
                        cudaStream_t st);

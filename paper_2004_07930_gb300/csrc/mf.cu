@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -198,6 +199,7 @@ __global__ void k_mf_inverse(const int* __restrict__ list, const int* __restrict
 
 template <typename V>
 static void tile_attrs_all();
+static void tc_pack_all(DevMF& mf, cudaStream_t st);
 
 void mf_factor(DevMF& mf, double tau_abs, cudaStream_t st) {
   if (mf.fp32)
@@ -227,7 +229,11 @@ void mf_factor(DevMF& mf, double tau_abs, cudaStream_t st) {
       { k_mf_inverse<double2><<<e - b, 256, shm, st>>>(mf.level_list + b, mf.k, mf.f, mf.Foff, mf.Moff, mf.Doff,
                                                      mf.F, (double2*)mf.M, (double2*)mf.MT, (double2*)mf.Dinv); count_launch(); }
   }
+  // tensor-core tiles: pack their factor blocks from X_t (forward) and X_t^T (backward)
+  if (mf.tc && mf.fp32) tc_pack_all(mf, st);
 }
+
+bool mf_tc_usable(const DevMF& mf, int s) { return mf.tc && mf.fp32 && s > 8 && s <= 64; }
 
 // ---------------------------------------------------------------------------
 // Solve sweeps
@@ -436,7 +442,321 @@ __global__ void k_mf_reduce(const int4* __restrict__ rblocks, int nrb, const int
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core tiles (complex FP32 form): the same tile product on tcgen05.
+//
+// The tile's factor block is packed once, after the factorisation, as
+// 16-column chunks; each chunk holds a real and an imaginary plane of
+// nr8 = roundup(rows, 8) rows x 16 reduction indices, TF32-rounded, in the
+// K-major layout of 8-row x 16-byte core matrices (a row group's 4 core
+// matrices are adjacent, row groups 512 bytes apart), reduction indices past
+// the tile's end zero. A chunk is two contiguous copies (cp.async.bulk) into
+// a two-stage shared-memory ring. The input rows are staged as two N x 128
+// operands, N = 2S: B1 = [Re b | Im b] and B2 = [-Im b | Re b], so that
+//   D = Re(M) B1^T + Im(M) B2^T = [Re(M b) | Im(M b)]
+// accumulates in TMEM (128 lanes = output rows, N columns, FP32). One thread
+// issues the MMAs (M = 128, N = 2S, K = 8 per instruction) and commits them
+// to the ring's barriers; every wait is bounded and a timeout sets tc_err.
+// Rows past the tile's end hold stale shared memory; their outputs are never
+// written.
+// ---------------------------------------------------------------------------
+constexpr int TC_PLANE = 8192;              // one plane of a 128-row chunk in shared memory
+constexpr int TC_STAGE = 2 * TC_PLANE;      // a chunk (real + imaginary plane)
+constexpr int TC_SBO_A = 4 * 128;           // row-group stride of a 16-column chunk
+constexpr int TC_SBO_B = (MF_TK / 4) * 128; // row-group stride of an N x 128 operand
+
+__device__ __forceinline__ uint32_t tc_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// shared-memory matrix descriptor: no swizzle, K-major, descriptor version 1
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (long it = 0; it < (1L << 24) && !done; ++it)
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ float tc_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+// byte offset of element (row, col) in a K-major core-matrix tile whose row
+// groups are sbo bytes apart
+__device__ __forceinline__ int tc_off(int row, int col, int sbo) {
+  return (row >> 3) * sbo + (col >> 2) * 128 + (row & 7) * 16 + (col & 3) * 4;
+}
+
+// tile geometry shared by the packer and the kernel
+struct TcGeom {
+  int t, r0, slot, f, k, nout, ld, kbeg, kstop, nr, nr8, nk, nch;
+};
+template <bool FWD>
+__device__ __forceinline__ TcGeom tc_geom(int4 tile, const int* kk, const int* ff) {
+  TcGeom g;
+  g.t = tile.x;
+  g.r0 = tile.y;
+  g.slot = tile.w;
+  g.f = ff[g.t];
+  g.k = kk[g.t];
+  g.nout = FWD ? g.f : g.k;
+  g.ld = FWD ? g.f : g.k;
+  const int kend = FWD ? ((g.r0 < g.k) ? min(g.k, g.r0 + MF_TILE) : g.k) : g.f;
+  g.kbeg = FWD ? tile.z : max(tile.z, g.r0);
+  g.kstop = min(kend, tile.z + MF_TK);
+  g.nr = min(MF_TILE, g.nout - g.r0);
+  g.nr8 = (g.nr + 7) & ~7;
+  g.nk = g.kstop - g.kbeg;
+  g.nch = (g.nk + 15) / 16;
+  return g;
+}
+
+// Pack the factor blocks of the tensor-core tiles (after k_mf_inverse).
+template <bool FWD>
+__global__ void k_tc_pack(const int4* __restrict__ tiles, const int64_t* __restrict__ off, const int* __restrict__ kk,
+                          const int* __restrict__ ff, const int64_t* __restrict__ Moff, const float2* __restrict__ M,
+                          unsigned char* __restrict__ TC) {
+  const TcGeom g = tc_geom<FWD>(tiles[blockIdx.x], kk, ff);
+  const float2* Mt = M + Moff[g.t];
+  unsigned char* base = TC + off[blockIdx.x];
+  const int plane = g.nr8 * 64;
+  const int64_t total = (int64_t)g.nch * 16 * g.nr8;
+  for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
+    const int m = (int)(i % g.nr8);
+    const int kc = (int)((i / g.nr8) % 16);
+    const int q = (int)(i / ((int64_t)g.nr8 * 16));
+    const int col = g.kbeg + q * 16 + kc;
+    float2 v = make_float2(0.f, 0.f);
+    if (m < g.nr && col < g.kstop) v = Mt[(g.r0 + m) + (int64_t)col * g.ld];
+    unsigned char* ch = base + (int64_t)q * 2 * plane;
+    const int o = tc_off(m, kc, TC_SBO_A);
+    *reinterpret_cast<float*>(ch + o) = tc_tf32(v.x);
+    *reinterpret_cast<float*>(ch + plane + o) = tc_tf32(v.y);
+  }
+}
+
+static void tc_pack_all(DevMF& mf, cudaStream_t st) {
+  if (mf.ftc_n)
+    { k_tc_pack<true><<<(unsigned)mf.ftc_n, 256, 0, st>>>(mf.ftiles_tc, mf.ftc_off, mf.k, mf.f, mf.Moff,
+                                                         (const float2*)mf.M, mf.TC); count_launch(); }
+  if (mf.btc_n)
+    { k_tc_pack<false><<<(unsigned)mf.btc_n, 256, 0, st>>>(mf.btiles_tc, mf.btc_off, mf.k, mf.f, mf.Moff,
+                                                          (const float2*)mf.MT, mf.TC); count_launch(); }
+}
+
+template <int S>
+static constexpr size_t tc_smem_bytes() {
+  return 2 * (size_t)(2 * S) * MF_TK * 4 + 2 * (size_t)TC_STAGE;
+}
+
+template <int S, bool FWD>
+__global__ void __launch_bounds__(MF_TILE) k_mf_tile_tc(
+    const int4* __restrict__ tiles, const int64_t* __restrict__ tcoff, const unsigned char* __restrict__ TC,
+    const int* __restrict__ kk, const int* __restrict__ ff, const int64_t* __restrict__ rowoff,
+    const int* __restrict__ rows, const int64_t* __restrict__ cptr, const int* __restrict__ cidx,
+    const int64_t* __restrict__ Doff, const float2* __restrict__ Dinv, float2* __restrict__ Xsub,
+    float2* __restrict__ Wout, float2* __restrict__ P, int s, int* __restrict__ err) {
+  constexpr int N = 2 * S;
+  constexpr int BT = N * MF_TK * 4;
+  constexpr uint32_t NCOL = N < 32 ? 32 : N;
+  extern __shared__ __align__(1024) unsigned char smem_tc[];
+  unsigned char* sB1 = smem_tc;
+  unsigned char* sB2 = smem_tc + BT;
+  unsigned char* stg = smem_tc + 2 * BT;
+  __shared__ __align__(8) uint64_t full[2], freeb[2], done;
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const TcGeom g = tc_geom<FWD>(tiles[blockIdx.x], kk, ff);
+  const unsigned char* src = TC + tcoff[blockIdx.x];
+  const uint32_t plane = (uint32_t)g.nr8 * 64, cbytes = 2 * plane;
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&freeb[i])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&done)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto load_chunk = [&](int q) {  // thread 0: chunk q into stage q & 1
+    const uint32_t bar = tc_smem(&full[q & 1]);
+    const uint32_t dst = tc_smem(stg + (q & 1) * TC_STAGE);
+    const unsigned char* c = src + (int64_t)q * cbytes;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(cbytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(c), "r"(plane), "r"(bar)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     dst + TC_PLANE),
+                 "l"(c + plane), "r"(plane), "r"(bar)
+                 : "memory");
+  };
+  if (tid == 0)
+    for (int q = 0; q < min(2, g.nch); ++q) load_chunk(q);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(&tslot)),
+                 "r"(NCOL));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // input rows -> B1 = [Re | Im], B2 = [-Im | Re] (TF32), zero past the tile's reduction end
+  const int64_t ro = rowoff[g.t];
+  if (tid < g.nch * 16) {
+    const int l = tid;
+    float2 v[S];
+#pragma unroll
+    for (int c = 0; c < S; ++c) v[c] = make_float2(0.f, 0.f);
+    if (l < g.nk) {
+      const int64_t R = ro + g.kbeg + l;
+      const int local = g.kbeg + l;
+      const float2* xs = (FWD || local >= g.k) ? Xsub + (int64_t)rows[R] * s : Wout + R * s;
+#pragma unroll
+      for (int c = 0; c < S; ++c)
+        if (c < s) v[c] = xs[c];
+      if (FWD) {
+        const int64_t pe = cptr[R + 1];
+        for (int64_t p = cptr[R]; p < pe; ++p) {
+          const float2* w = Wout + (int64_t)cidx[p] * s;
+#pragma unroll
+          for (int c = 0; c < S; ++c)
+            if (c < s) v[c] = make_float2(v[c].x + w[c].x, v[c].y + w[c].y);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < S; ++c) {
+      const float re = tc_tf32(v[c].x), im = tc_tf32(v[c].y);
+      *reinterpret_cast<float*>(sB1 + tc_off(c, l, TC_SBO_B)) = re;
+      *reinterpret_cast<float*>(sB1 + tc_off(S + c, l, TC_SBO_B)) = im;
+      *reinterpret_cast<float*>(sB2 + tc_off(c, l, TC_SBO_B)) = -im;
+      *reinterpret_cast<float*>(sB2 + tc_off(S + c, l, TC_SBO_B)) = re;
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t taddr = tslot;
+  // kind::tf32: D f32, A and B tf32, both K-major, N = 2S, M = 128
+  constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  bool ok = true;
+  if (tid == 0) {
+    for (int q = 0; q < g.nch && ok; ++q) {
+      const int sidx = q & 1;
+      const uint32_t ph = (q >> 1) & 1;
+      ok = tc_wait(tc_smem(&full[sidx]), ph);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t aRe = tc_smem(stg + sidx * TC_STAGE), aIm = aRe + TC_PLANE;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const uint64_t dRe = tc_desc(aRe + j * 256, 128, TC_SBO_A);
+        const uint64_t dIm = tc_desc(aIm + j * 256, 128, TC_SBO_A);
+        const uint32_t kb = (uint32_t)(q * 4 + 2 * j) * 128;
+        const uint64_t d1 = tc_desc(tc_smem(sB1) + kb, 128, TC_SBO_B);
+        const uint64_t d2 = tc_desc(tc_smem(sB2) + kb, 128, TC_SBO_B);
+        const uint32_t acc = (q > 0 || j > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(taddr),
+            "l"(dRe), "l"(d1), "r"(idesc), "r"(acc));
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(taddr),
+            "l"(dIm), "l"(d2), "r"(idesc), "r"(1u));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       tc_smem(&freeb[sidx]))
+                   : "memory");
+      if (q + 2 < g.nch) {
+        ok = tc_wait(tc_smem(&freeb[sidx]), ph);  // the MMAs reading this stage have completed
+        if (!ok) break;
+        load_chunk(q + 2);
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     tc_smem(&done))
+                 : "memory");
+  }
+  __syncwarp();
+  const bool fin = tc_wait(tc_smem(&done), 0);
+  if (!fin || !ok) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (fin) {
+    const int m = tid;  // TMEM lane = output row of the tile
+    const bool act = m < g.nr;
+    const int rr = g.r0 + m;
+    const int64_t Rg = ro + rr;
+    const uint32_t lane_base = taddr + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+    for (int g16 = 0; g16 < S / 16; ++g16) {
+      uint32_t re[16], im[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]), "=r"(re[6]), "=r"(re[7]),
+            "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]), "=r"(re[12]), "=r"(re[13]), "=r"(re[14]),
+            "=r"(re[15])
+          : "r"(lane_base + g16 * 16));
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]), "=r"(im[6]), "=r"(im[7]),
+            "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]), "=r"(im[12]), "=r"(im[13]), "=r"(im[14]),
+            "=r"(im[15])
+          : "r"(lane_base + S + g16 * 16));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (!act) continue;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int c = g16 * 16 + u;
+        if (c >= s) break;
+        float2 a = make_float2(__uint_as_float(re[u]), __uint_as_float(im[u]));
+        if (g.slot >= 0) {
+          P[((int64_t)g.slot * MF_TILE + m) * s + c] = a;
+        } else if (FWD) {
+          if (rr < g.k) {
+            Wout[Rg * s + c] = c_mul(a, Dinv[Doff[g.t] + rr]);
+          } else {
+            const int64_t pe = cptr[Rg + 1];
+            for (int64_t p = cptr[Rg]; p < pe; ++p) a = c_add(a, Wout[(int64_t)cidx[p] * s + c]);
+            Wout[Rg * s + c] = a;
+          }
+        } else {
+          Xsub[(int64_t)rows[Rg] * s + c] = a;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(NCOL));
+}
+
 static inline unsigned blocks_for(int64_t work, int b) { return (unsigned)((work + b - 1) / b); }
+
+template <typename V, int S>
+static constexpr bool tc_width() {
+  return std::is_same<V, float2>::value && S >= 16;
+}
+
+template <typename V, int S, bool FWD>
+static void tc_launch(DevMF& mf, int l, V* Xsub, int s, cudaStream_t st) {
+  if constexpr (tc_width<V, S>()) {
+    const int* ptr = FWD ? mf.ftc_ptr_h : mf.btc_ptr_h;
+    const int tb = ptr[l], te = ptr[l + 1];
+    if (te > tb) {
+      k_mf_tile_tc<S, FWD><<<te - tb, MF_TILE, tc_smem_bytes<S>(), st>>>(
+          (FWD ? mf.ftiles_tc : mf.btiles_tc) + tb, (FWD ? mf.ftc_off : mf.btc_off) + tb, mf.TC, mf.k, mf.f,
+          mf.rowoff, mf.rows, mf.cptr, mf.cidx, mf.Doff, (const float2*)mf.Dinv, (float2*)Xsub, (float2*)mf.Wout,
+          (float2*)mf.P, s, mf.tc_err);
+      count_launch();
+    }
+  }
+}
 
 template <typename V, int S>
 static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
@@ -446,21 +766,31 @@ static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
   const V* M = (const V*)mf.M;
   const V* MT = (const V*)mf.MT;
   const V* Dv = (const V*)mf.Dinv;
+  // with the tensor cores on, each level's tiles are split between the
+  // tcgen05 kernel and the SIMT kernel (the tiles the SIMT kernel keeps are
+  // the small ones); both write the same partial slots and epilogues
+  const bool tc = tc_width<V, S>() && mf.tc;
+  const int* fptr = tc ? mf.fs_ptr_h : mf.ftile_ptr_h;
+  const int* bptr = tc ? mf.bs_ptr_h : mf.btile_ptr_h;
+  const int4* ftl = tc ? mf.ftiles_s : mf.ftiles;
+  const int4* btl = tc ? mf.btiles_s : mf.btiles;
   for (int l = 0; l < mf.nlevels; ++l) {
-    const int tb = mf.ftile_ptr_h[l], te = mf.ftile_ptr_h[l + 1];
+    const int tb = fptr[l], te = fptr[l + 1];
     if (te > tb)
-      { k_mf_tile<V, S, true><<<te - tb, MF_TILE, shm, st>>>(mf.ftiles + tb, mf.k, mf.f, mf.rowoff, mf.Moff, M, mf.rows,
+      { k_mf_tile<V, S, true><<<te - tb, MF_TILE, shm, st>>>(ftl + tb, mf.k, mf.f, mf.rowoff, mf.Moff, M, mf.rows,
                                                              mf.cptr, mf.cidx, mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
+    if (tc) tc_launch<V, S, true>(mf, l, Xsub, s, st);
     const int rb = mf.frb_ptr_h[l], re = mf.frb_ptr_h[l + 1];
     if (re > rb)
       { k_mf_reduce<V, true><<<blocks_for((int64_t)(re - rb) * MF_TILE * s, 256), 256, 0, st>>>(
           mf.frb + rb, re - rb, mf.k, mf.f, mf.rowoff, mf.Doff, mf.rows, mf.cptr, mf.cidx, Dv, Wout, P, Xsub, s); count_launch(); }
   }
   for (int l = mf.nlevels - 1; l >= 0; --l) {
-    const int tb = mf.btile_ptr_h[l], te = mf.btile_ptr_h[l + 1];
+    const int tb = bptr[l], te = bptr[l + 1];
     if (te > tb)
-      { k_mf_tile<V, S, false><<<te - tb, MF_TILE, shm, st>>>(mf.btiles + tb, mf.k, mf.f, mf.rowoff, mf.Moff, MT,
+      { k_mf_tile<V, S, false><<<te - tb, MF_TILE, shm, st>>>(btl + tb, mf.k, mf.f, mf.rowoff, mf.Moff, MT,
                                                               mf.rows, mf.cptr, mf.cidx, mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
+    if (tc) tc_launch<V, S, false>(mf, l, Xsub, s, st);
     const int rb = mf.brb_ptr_h[l], re = mf.brb_ptr_h[l + 1];
     if (re > rb)
       { k_mf_reduce<V, false><<<blocks_for((int64_t)(re - rb) * MF_TILE * s, 256), 256, 0, st>>>(
@@ -475,6 +805,11 @@ static void tile_attrs() {
   const int shm = (int)tile_smem_bytes<V, S>();
   cudaFuncSetAttribute(k_mf_tile<V, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
   cudaFuncSetAttribute(k_mf_tile<V, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+  if constexpr (tc_width<V, S>()) {
+    const int tshm = (int)tc_smem_bytes<S>();
+    cudaFuncSetAttribute(k_mf_tile_tc<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tshm);
+    cudaFuncSetAttribute(k_mf_tile_tc<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tshm);
+  }
 }
 
 #define HZ_TILE_WIDTHS(X) X(1) X(2) X(4) X(8) X(16) X(32) X(64)

@@ -34,7 +34,7 @@ class HzOptions(C.Structure):
     _fields_ = [("precision", C.c_int32), ("rtol", C.c_double), ("maxit", C.c_int32), ("restart", C.c_int32),
                 ("max_block", C.c_int32), ("coarse_mode", C.c_int32), ("coarse_inner_its", C.c_int32),
                 ("leaf_size", C.c_int32), ("pivot_tau", C.c_double), ("verbose", C.c_int32),
-                ("use_graphs", C.c_int32)]
+                ("use_graphs", C.c_int32), ("tensor_cores", C.c_int32)]
 
 
 class HzStats(C.Structure):
