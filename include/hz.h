@@ -209,7 +209,8 @@ int hz_profile_end(hz_ctx* ctx, hz_phase_time* out, int32_t cap, int32_t* count)
  * listed in done_ids (up to cap per step) and read once with
  * hz_server_fetch (u [ns][n][2] host doubles; HZ_ENOTCONV if a column stopped
  * at maxit). Steps of servers of different contexts may be interleaved; a
- * server and its context are not thread-safe. Errors: HZ_EINVAL (bad
+ * server and its context are not thread-safe. Free a server (hz_server_free)
+ * before its context (hz_free). Errors: HZ_EINVAL (bad
  * argument, unknown or unfinished request, duplicate id, source outside the
  * mesh), HZ_ENOMEM, HZ_ECUDA. */
 typedef struct hz_server hz_server;
