@@ -14,7 +14,7 @@ Sec. "Domain decomposition preconditioner":
 
 Readings where the text is silent (the library follows the same ones):
 overlap = the non-overlapping element set plus every element that shares a
-mesh vertex with it; D_i is Boolean ownership by the lowest-index
+mesh vertex with it (one layer; `overlap` layers repeat the rule); D_i is Boolean ownership by the lowest-index
 non-overlapping subdomain whose elements carry the dof; A_i is assembled
 over the elements of Gamma_i with -i omega sqrt(m_e) B_f on physical Robin
 faces and on faces of the boundary of Gamma_i interior to Omega, and keeps
@@ -35,13 +35,16 @@ from . import assemble as oa
 from . import p3
 
 
-def overlap_elements(tets, part, i):
-    """Elements of part i plus every element sharing a vertex with them."""
+def overlap_elements(tets, part, i, layers=1):
+    """Elements of part i grown by `layers` element layers: each layer adds
+    every element that shares a vertex with the current set."""
     tets = np.asarray(tets)
-    own = np.nonzero(part == i)[0]
-    verts = np.zeros(tets.max() + 1, dtype=bool)
-    verts[tets[own].ravel()] = True
-    return np.nonzero(verts[tets].any(axis=1))[0]
+    inset = np.asarray(part) == i
+    for _ in range(layers):
+        verts = np.zeros(tets.max() + 1, dtype=bool)
+        verts[tets[inset].ravel()] = True
+        inset = verts[tets].any(axis=1)
+    return np.nonzero(inset)[0]
 
 
 def ownership(space, part, nparts):
@@ -105,14 +108,14 @@ def local_matrix(space, velocity, freq, elems, bfaces, btags, dir_dofs):
 class OneLevelORAS:
     """Eq. oras with exact local solves (SuperLU)."""
 
-    def __init__(self, space, velocity, freq, bfaces, btags, part, nparts):
+    def __init__(self, space, velocity, freq, bfaces, btags, part, nparts, overlap=1):
         part = np.asarray(part)
         self.n = space.n
         owner = ownership(space, part, nparts)
         dd = space.dirichlet_dofs(bfaces, btags)
         self.subs = []
         for i in range(nparts):
-            elems = overlap_elements(space.tets, part, i)
+            elems = overlap_elements(space.tets, part, i, overlap)
             dofs, Ai = local_matrix(space, velocity, freq, elems, bfaces, btags, dd)
             Di = (owner[dofs] == i).astype(np.float64)
             self.subs.append((dofs, Di, Ai, spla.splu(Ai.tocsc())))
@@ -229,13 +232,13 @@ class TwoLevel:
     """Eq. 2lvl on top of Eq. oras; coarse solve exact ('direct') or by
     `inner_its` GMRES iterations with coarse one-level ORAS ('gmres')."""
 
-    def __init__(self, prob, coarse_mode="gmres", inner_its=10):
+    def __init__(self, prob, coarse_mode="gmres", inner_its=10, overlap=1):
         fine, coarse = prob["fine"], prob["coarse"]
         self.space = oa.P3Space(fine["xyz"], fine["tets"])
         A, dd = oa.assemble(self.space, prob["velocity"], prob["freq"], fine["bfaces"], fine["btags"])
         self.A, _ = oa.apply_dirichlet(A, None, dd)
         self.fine_oras = OneLevelORAS(self.space, prob["velocity"], prob["freq"], fine["bfaces"],
-                                      fine["btags"], prob["elem_part"], prob["nparts"])
+                                      fine["btags"], prob["elem_part"], prob["nparts"], overlap)
         self.mode = coarse_mode
         self.inner_its = inner_its
         if coarse_mode == "none":
@@ -251,7 +254,7 @@ class TwoLevel:
                                                       prob["velocity"])
         self.part_c, self.vel_c = part_c, vel_c
         oras_c = OneLevelORAS(self.space_c, vel_c, prob["freq"], coarse["bfaces"], coarse["btags"],
-                              part_c, prob["nparts"])
+                              part_c, prob["nparts"], overlap)
         self.coarse_oras = oras_c
 
     def coarse_apply_M(self, rH):
