@@ -37,8 +37,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-FP64_NOMINAL_GFLOPS = 1250.0  # nominal GB300 FP64 rate (no FP64 figure in the measured peaks)
-FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock = 80.5 TFLOP/s
+FP64_NOMINAL_GFLOPS = 1250.0  # nominal GB300 FP64 rate, context only (the FP64 peak is measured live)
 TILE_PROFILE = os.path.join(ROOT, "profiles", "k_mf_tile_overthrust5_quarter.md")
 
 
@@ -60,6 +59,49 @@ def fronts_traffic(cfg, per_app):
     return None
 
 
+def fp32_simt_tflops(torch, sm_max_mhz):
+    """FP32 SIMT peak derived from the device: SMs (queried) x 128 FP32 lanes
+    x 2 flops per FMA x the maximum SM clock (MEASURED_PEAKS.json)."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = sm_max_mhz or 2070.0
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, sms, mhz
+
+
+def measure_gemm_peaks(torch):
+    """Live GEMM rates on this GPU (cuBLAS through torch.matmul, best of 5
+    after warm-up, CUDA events): FP64 (DGEMM), FP32 without TF32 (SGEMM) and
+    TF32 tensor-core GEMM, N = 8192 (FP64: 4096). They are the measured
+    denominators of the FP64 and FP32 rooflines."""
+    out = {}
+    old = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for name, dt, n, tf32 in (("fp64_gemm_tflops", torch.float64, 4096, False),
+                                  ("fp32_gemm_tflops", torch.float32, 8192, False),
+                                  ("tf32_gemm_tflops", torch.float32, 8192, True)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            a = torch.randn(n, n, dtype=dt, device="cuda")
+            b = torch.randn(n, n, dtype=dt, device="cuda")
+            for _ in range(2):
+                torch.matmul(a, b)
+            best = None
+            for _ in range(5):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            out[name] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
+    torch.cuda.empty_cache()
+    out["how"] = "torch.matmul (cuBLAS), square N=8192 (FP64 N=4096), best of 5 after 2 warm-up, CUDA events"
+    return out
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -72,7 +114,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the FP64 form")
     ap.add_argument("--fp64-warmup", type=int, default=1, help="warm-up steps of the FP64 form")
-    ap.add_argument("--variants", default="one_level", help="extra preconditioner variants of the headline form")
+    ap.add_argument("--variants", default="one_level,coarse_fp32",
+                    help="extra variants of the headline form: one_level (one-level ORAS; also runs the short "
+                         "serving stream), coarse_fp32 (mixed form with the coarse level in complex FP32)")
     ap.add_argument("--maxit", type=int, default=500, help="FGMRES iteration cap (lower it only for profiling runs)")
     ap.add_argument("--coarse", choices=["gmres", "none", "direct"], default="gmres",
                     help="coarse level of the headline forms (the paper's: gmres, 10 inner steps)")
@@ -260,7 +304,32 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, **opts):
+def serving_stream(S, hz, rhs_per_s, nreq=24, load=0.8, seed=11):
+    """A short seeded Poisson stream through the continuous-batching server
+    on the solver S: nreq requests of 1-16 point sources at uniform surface
+    positions (z = 100 m), offered at `load` x the measured saturated rate
+    rhs_per_s. Returns RHS/s and p50/p99 latency (arrival to completion)."""
+    import numpy as np
+
+    from paper_2004_07930_gb300.serve import ServingLoop
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nsrc = rng.integers(1, 17, nreq)
+    rate = load * rhs_per_s / nsrc.mean()           # requests per second
+    arrival = np.cumsum(rng.exponential(1.0 / rate, nreq))
+    reqs = []
+    for i in range(nreq):
+        xy = rng.uniform(1000.0, 19000.0, size=(nsrc[i], 2))
+        reqs.append((float(arrival[i]), i, 0, np.concatenate([xy, np.full((nsrc[i], 1), 100.0)], axis=1)))
+    loop = ServingLoop({0: S}, 32)
+    summ = loop.run_stream(reqs)
+    loop.close()
+    summ.update({"offered_load": load, "offered_rhs_per_s": load * rhs_per_s, "slots": 32,
+                 "stream": "%d requests, 1-16 sources each, Poisson arrivals (PCG64 seed %d)" % (nreq, seed)})
+    return summ
+
+
+def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, serve=False, **opts):
     prec = hz.HZ_PREC_MIXED if form == "mixed" else hz.HZ_PREC_FP64
     if TENSOR_CORES >= 0:
         opts["tensor_cores"] = TENSOR_CORES
@@ -297,7 +366,8 @@ def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, **o
     res = {"rhs_per_s": ns * steps * ws / (ms / 1e3), "ms_per_step": ms / steps, "steps": steps, "warmup": warmup,
            "iterations": [s["iterations"] for s in stats], "max_rel_residual": max(s["max_rel_residual"] for s in stats),
            "converged": all(s["converged"] for s in stats), "setup_s": setup_wall,
-           "factor_s": stats[0]["factor_seconds"], "info": info, "phases": prof, "gpu_launches": launches}
+           "factor_s": stats[0]["factor_seconds"], "info": info, "phases": prof, "gpu_launches": launches,
+           "coarse_fp32": S.options.coarse_fp32, "overlap": S.options.overlap}
     if with_e2e:
         import numpy as np
 
@@ -312,6 +382,10 @@ def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, **o
         res["e2e"] = {"value": ns * steps * ws / el, "unit": "RHS/s",
                       "h2d_bytes_per_step": int(src.size * 8 + ns * 16),
                       "d2h_bytes_per_step": int(hostbuf.nbytes)}
+    if serve:
+        res["serving"] = serving_stream(S, hz, res["rhs_per_s"])
+        res["serving"]["preconditioner"] = "one-level ORAS" if opts.get("coarse_mode") == hz.HZ_COARSE_NONE else \
+            "two-level ORAS"
     S.close()
     return res
 
@@ -458,60 +532,78 @@ def main():
     for v in [x for x in args.variants.split(",") if x]:
         if v == "one_level":
             variants["one_level_" + forms[0]] = measure_form(prob, forms[0], args.steps, args.warmup, stream, ws,
-                                                             torch, hz, False, coarse_mode=hz.HZ_COARSE_NONE)
+                                                             torch, hz, False, coarse_mode=hz.HZ_COARSE_NONE,
+                                                             serve=(forms[0] == "mixed" and ws == 1))
+        elif v == "coarse_fp32" and forms[0] == "mixed" and args.coarse != "none":
+            variants["coarse_fp32_mixed"] = measure_form(prob, "mixed", args.steps, args.warmup, stream, ws, torch,
+                                                         hz, False, coarse_mode=cm, coarse_fp32=1)
     head = forms[0]
     r = results[head]
-    hbm, peak_kind, _ = peaks()
+    hbm, peak_kind, sm_max = peaks()
+    gemm = measure_gemm_peaks(torch)
+    simt, nsm, mhz = fp32_simt_tflops(torch, sm_max)
     ph = r["phases"]["fronts"]
     per_app = ph["bytes"] / ph["calls"]  # algorithmic bytes of one application of the fine local solves
     hbm_achieved = ph["bytes"] / (ph["ms"] / 1e3) / 1e9
+    flops_achieved = ph["flops"] / (ph["ms"] / 1e3) / 1e12
     tc_on = (TENSOR_CORES if TENSOR_CORES >= 0 else hz.default_options().tensor_cores) == 1
-    if head == "mixed" and tc_on:
-        # tcgen05 sweeps: the tensor rate is far above what 8 bytes per factor entry can feed,
-        # so the roof is HBM; the DRAM traffic of these kernels has not been captured with ncu
+    if head == "mixed":
+        kern = ("fine local solves (tcgen05 sweep tiles, 3xTF32 split, FP32 accumulation in TMEM)" if tc_on else
+                "fine local solves (SIMT complex FP32 sweep tiles)")
+        # a sweep reads each factor entry once per application: HBM is the roof of the
+        # tensor-core form; the SIMT FP32 rate (16 flops per factor byte at s = 16) is given beside it
         roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm, "unit": "GB/s", "frac": hbm_achieved / hbm,
-                "traffic": None, "traffic_unit": "bytes per application of the fine local solves",
-                "kernel": "fine local solves (k_mf_tile_tc on tcgen05 + k_mf_tile for small tiles + k_mf_reduce, "
-                          "TF32 factors, FP32 accumulation)",
-                "peak_kind": peak_kind, "algorithmic_bytes_per_application": per_app,
-                "fp32_tflops_achieved": ph["flops"] / (ph["ms"] / 1e3) / 1e12, "launches": ph["calls"]}
-    elif head == "mixed":
-        # s = 16 puts the FP32 sweeps above the SIMT FP32 ridge (16 flops per factor byte), so the
-        # binding roof is the FP32 FMA rate; the HBM figures are reported beside it
-        achieved = ph["flops"] / (ph["ms"] / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_SIMT_TFLOPS,
-                "traffic": fronts_traffic(args.config, per_app),
-                "traffic_unit": "bytes per application of the fine local solves",
-                "kernel": "fine local solves (k_mf_tile + k_mf_reduce, complex FP32)",
-                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
-                "hbm_achieved_gbs": hbm_achieved, "hbm_peak_gbs": hbm, "hbm_frac": hbm_achieved / hbm,
-                "hbm_peak_kind": peak_kind, "algorithmic_bytes_per_application": per_app,
-                "launches": ph["calls"]}
+                "traffic": None if tc_on else fronts_traffic(args.config, per_app),
+                "traffic_unit": "DRAM bytes per application of the fine local solves",
+                "kernel": kern, "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_application": per_app, "applications": ph["calls"],
+                "fp32_tflops_achieved": flops_achieved, "fp32_simt_peak_tflops": simt,
+                "fp32_simt_frac": flops_achieved / simt,
+                "fp32_simt_peak_kind": "derived: %d SMs (queried) x 128 FP32 lanes x 2 x %.0f MHz" % (nsm, mhz)}
     else:
-        achieved = ph["flops"] / (ph["ms"] / 1e3) / 1e9
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
-                "frac": achieved / FP64_NOMINAL_GFLOPS, "traffic": None,
-                "kernel": "fine local solves (k_mf_tile + k_mf_reduce, complex FP64)",
-                "peak_kind": "nominal FP64", "hbm_achieved_gbs": hbm_achieved, "launches": ph["calls"]}
+        fp64 = gemm["fp64_gemm_tflops"]
+        roof = {"bound": "alu", "achieved": flops_achieved, "peak": fp64, "unit": "TFLOP/s",
+                "frac": flops_achieved / fp64, "traffic": None,
+                "kernel": "fine local solves (SIMT complex FP64 sweep tiles)",
+                "peak_kind": "measured live: FP64 DGEMM (cuBLAS, torch.matmul)", "hbm_achieved_gbs": hbm_achieved,
+                "hbm_frac": hbm_achieved / hbm, "applications": ph["calls"]}
+    phase_roof = {}
+    for name, q in r["phases"].items():
+        if q["calls"] and q["ms"] > 0:
+            gbs = q["bytes"] / (q["ms"] / 1e3) / 1e9
+            phase_roof[name] = {"share_of_step": q["ms"] / (r["ms_per_step"] * r["steps"]), "ms_per_call": q["ms"] / q["calls"],
+                                "gbs": gbs, "hbm_frac": gbs / hbm,
+                                "tflops": q["flops"] / (q["ms"] / 1e3) / 1e12}
+    if head == "mixed":
+        cf = results[head].get("coarse_fp32", 0)
+        dtype = ("c64 fine fronts (" + ("3xTF32 tensor cores" if tc_on else "SIMT FP32") + ") + " +
+                 ("c64 coarse level + " if cf else "c128 coarse level + ") + "c128 Krylov/SpMM/outer residual")
+    else:
+        dtype = "c128"
     line = {
         "metric": "RHS solved/s at rtol 1e-6", "value": r["rhs_per_s"], "unit": "RHS/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": ("tf32 x fp32 tensor-core fronts" if tc_on else "c64 fronts") + " + c128 Krylov/SpMM/coarse"
-                 if head == "mixed" else "c128",
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype,
         "data": "synthetic (seeded Overthrust-like model; no real data)",
         "config": {"workload": desc, "n": r["info"]["n"], "nnz": r["info"]["nnz"], "sources_per_step": 16,
-                   "rtol": 1e-6, "l2_flush": "inputs larger than L2 (factors %.1f GB)" %
+                   "rtol": 1e-6, "preconditioner": {"gmres": "two-level ORAS, coarse by 10 GMRES steps",
+                                                    "none": "one-level ORAS", "direct": "two-level ORAS, direct coarse"}[args.coarse],
+                   "l2_flush": "inputs larger than L2 (factors %.1f GB)" %
                    (r["info"]["device_bytes"] / 1e9), "parallelism": "replicas x%d (sources)" % ws},
         "roofline": roof,
+        "phase_roofline": phase_roof,
+        "peaks": dict(gemm, hbm_gbs=hbm, hbm_kind=peak_kind, fp32_simt_derived_tflops=simt, sms=nsm),
         "clocks": clk,
         "gpu_launches": r["gpu_launches"],
         "e2e": r.get("e2e"),
         "forms": {f: {k: v for k, v in results[f].items() if k not in ("info",)} for f in results},
     }
     if variants:
-        line["variants"] = {k: {kk: vv for kk, vv in v.items() if kk not in ("info",)} for k, v in variants.items()}
+        line["variants"] = {k: {kk: vv for kk, vv in v.items() if kk not in ("info", "serving")}
+                            for k, v in variants.items()}
+        for v in variants.values():
+            if v.get("serving"):
+                line["serving"] = v["serving"]
     if "mixed" in results and "fp64" in results:
         line["mixed_over_fp64"] = results["mixed"]["rhs_per_s"] / results["fp64"]["rhs_per_s"]
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

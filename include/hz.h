@@ -93,6 +93,14 @@ typedef struct hz_options {
   int32_t tensor_cores;     /* mixed form only. 1: front-sweep tiles of at least 32 rows and 32 reduction
                                indices run on the tcgen05 tensor cores (factors rounded to TF32, FP32
                                accumulation) for blocks of 9-64 columns; 0 (default): SIMT FP32 sweeps */
+  int32_t overlap;          /* element layers added around each subdomain, each layer = every element
+                               sharing a vertex with the current set (1, the default; >= 1) */
+  int32_t coarse_fp32;      /* mixed form only. 0 (default): the coarse level (E, the coarse local factors,
+                               the inner coarse GMRES) is applied in FP64 as in the FP64 form; 1: the whole
+                               of M^{-1}, coarse level included, runs on complex FP32 blocks */
+  int32_t debug_bounds;     /* 1: after the factorisation, one device pass checks every index map of the
+                               hot path (restriction, ownership, front rows, extend-add sources, tiles)
+                               against its bounds; a violation fails hz_setup with HZ_EINTERNAL. 0 (default) */
 } hz_options;
 
 typedef struct hz_stats {
@@ -104,6 +112,7 @@ typedef struct hz_stats {
   double solve_seconds;     /* wall time of the solve call */
   double setup_seconds;     /* wall time of hz_setup (host + device) */
   double factor_seconds;    /* device factorisation time inside hz_setup */
+  int32_t perturbed_pivots; /* static pivot perturbations of the context's factorisations */
 } hz_stats;
 
 typedef struct hz_info {
@@ -161,6 +170,16 @@ int hz_get_info(const hz_ctx* ctx, hz_info* info);
 int hz_solve(hz_ctx* ctx, const double* src_xyz, const double* src_amp, int32_t ns, double* u,
              int32_t u_on_device, hz_stats* stats);
 
+/* Per-column results of the last hz_solve / hz_solve_rhs / hz_fwi_gradient call
+ * on ctx, in source order (for hz_fwi_gradient: the forward solves, then the
+ * adjoint ones): the true relative residual ||b - A u|| / ||b|| of each column
+ * when the call returned, and the FGMRES iterations that column used (its own
+ * accepted Arnoldi steps). rel_residual and iterations are caller-owned
+ * arrays of cap entries (either may be NULL); *ncols receives the number of
+ * columns of that call, which may exceed cap (only cap entries are written).
+ * Errors: HZ_EINVAL. */
+int hz_column_stats(const hz_ctx* ctx, double* rel_residual, int32_t* iterations, int32_t cap, int32_t* ncols);
+
 /* Same for given right-hand sides F [ns][n][2] (host or device). */
 int hz_solve_rhs(hz_ctx* ctx, const double* F, int32_t ns, int32_t F_on_device, double* u, int32_t u_on_device,
                  hz_stats* stats);
@@ -205,9 +224,11 @@ int hz_profile_end(hz_ctx* ctx, hz_phase_time* out, int32_t cap, int32_t* count)
  * together, and retires the slots whose true residual reached rtol (or that
  * used maxit iterations). Each column has its own Krylov space and its
  * arithmetic does not depend on the other columns, so a request's
- * wavefields are the same alone and in any mix. Finished requests are
- * listed in done_ids (up to cap per step) and read once with
- * hz_server_fetch (u [ns][n][2] host doubles; HZ_ENOTCONV if a column stopped
+ * wavefields are the same alone and in any mix. The ids of finished
+ * requests are written to done_ids, oldest first, at most cap per call (*ndone
+ * of them); ids that do not fit are kept and returned by the next
+ * hz_server_step calls, which return them even when no slot is active. Each
+ * finished request is read once with hz_server_fetch (u [ns][n][2] host doubles; HZ_ENOTCONV if a column stopped
  * at maxit). Steps of servers of different contexts may be interleaved; a
  * server and its context are not thread-safe. Free a server (hz_server_free)
  * before its context (hz_free). Errors: HZ_EINVAL (bad
@@ -263,14 +284,16 @@ int hz_matrix_csr(const hz_ctx* ctx, int64_t* rowptr, int32_t* col, double* val)
  *   stream cudaStream_t the kernels are queued on (NULL: legacy default
  *          stream); the call returns without waiting for them
  * Its two [n][s] work blocks live in a file-scope device array of
- * 2 x HZ_NOALLOC_MAX_ENTRIES complex values (32 MiB) that every GPU loading
- * the library holds until the process exits; the call allocates nothing.
- * n * s > HZ_NOALLOC_MAX_ENTRIES is refused with HZ_EINVAL before any launch.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture. All calls share the array: calls whose kernels overlap on the GPU
- * (other streams, other threads, other contexts) race. Every call overwrites
- * the entries it reads, so no state carries over between calls. */
+ * 2 x HZ_NOALLOC_MAX_ENTRIES complex values (32 MiB). hz_setup, with the
+ * context's device current, looks up the array's device address and keeps it
+ * in the context; that lookup loads the array on the device (it then stays
+ * there until the process exits), so the calls themselves allocate nothing.
+ * The current device must be the one hz_setup ran on, else HZ_EINVAL.
+ * n * s > HZ_NOALLOC_MAX_ENTRIES is refused with HZ_EINVAL before any launch;
+ * HZ_ECUDA if hz_setup could not look the array up. All calls share the
+ * array: calls whose kernels overlap on the GPU (other streams, other
+ * threads, other contexts) race. Every call overwrites the entries it reads,
+ * so no state carries over between calls. */
 #define HZ_NOALLOC_MAX_ENTRIES 1048576
 int hz_apply_A_noalloc(hz_ctx* ctx, const double* X, double* Y, int32_t s, void* stream);
 

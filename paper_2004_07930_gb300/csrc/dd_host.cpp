@@ -24,7 +24,7 @@ namespace hz {
 // Overlapping subdomains and local matrices
 // ---------------------------------------------------------------------------
 std::vector<Subdomain> build_subdomains(const Mesh& m, const Space& sp, const std::vector<int32_t>& part,
-                                        int nparts, const std::vector<double>& mvals, double omega) {
+                                        int nparts, const std::vector<double>& mvals, double omega, int layers) {
   const int64_t ne = m.ne, n = sp.n;
   std::vector<int32_t> owner(n, nparts);
   for (int64_t e = 0; e < ne; ++e)
@@ -37,19 +37,21 @@ std::vector<Subdomain> build_subdomains(const Mesh& m, const Space& sp, const st
   std::vector<uint8_t> vmark(m.nv), inset(ne);
   for (int i = 0; i < nparts; ++i) {
     Subdomain& S = subs[i];
-    std::fill(vmark.begin(), vmark.end(), 0);
-    std::fill(inset.begin(), inset.end(), 0);
-    for (int64_t e = 0; e < ne; ++e)
-      if (part[e] == i)
-        for (int a = 0; a < 4; ++a) vmark[m.tets[4 * e + a]] = 1;
-    for (int64_t e = 0; e < ne; ++e) {
-      bool hit = false;
-      for (int a = 0; a < 4; ++a) hit |= vmark[m.tets[4 * e + a]] != 0;
-      if (hit) {
-        S.elems.push_back(e);
-        inset[e] = 1;
+    // each layer adds every element sharing a vertex with the current set
+    for (int64_t e = 0; e < ne; ++e) inset[e] = part[e] == i;
+    for (int layer = 0; layer < layers; ++layer) {
+      std::fill(vmark.begin(), vmark.end(), 0);
+      for (int64_t e = 0; e < ne; ++e)
+        if (inset[e])
+          for (int a = 0; a < 4; ++a) vmark[m.tets[4 * e + a]] = 1;
+      for (int64_t e = 0; e < ne; ++e) {
+        bool hit = false;
+        for (int a = 0; a < 4; ++a) hit |= vmark[m.tets[4 * e + a]] != 0;
+        inset[e] = hit;
       }
     }
+    for (int64_t e = 0; e < ne; ++e)
+      if (inset[e]) S.elems.push_back(e);
     if (S.elems.empty()) throw HzError{1, "empty subdomain in the partition"};
     for (int64_t e : S.elems)
       for (int q = 0; q < NLOC; ++q) S.dofs.push_back(sp.l2g[NLOC * e + q]);

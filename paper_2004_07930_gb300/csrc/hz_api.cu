@@ -340,6 +340,9 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
   mf.row_local = pool.upload(row_local, st);
   mf.cptr = pool.upload(cptr, st);
   mf.cidx = pool.upload(cidx, st);
+  mf.cidx_n = (int64_t)cidx.size();
+  mf.ftiles_n = (int64_t)ftiles.size();
+  mf.btiles_n = (int64_t)btiles.size();
   mf.fp32 = fp32 ? 1 : 0;
   mf.M_total = Moff[nf];
   mf.D_total = Doff[nf];
@@ -409,7 +412,7 @@ void upload_split(const CsrC& A, DevSplitCsr& D, DevPool& pool, cudaStream_t st,
 }
 
 struct DevReal {
-  int64_t n = 0;
+  int64_t n = 0, nnz = 0;
   int64_t* rp = nullptr;
   int32_t* col = nullptr;
   double* val = nullptr;
@@ -417,6 +420,7 @@ struct DevReal {
 };
 void upload_real(const CsrR& A, DevReal& D, DevPool& pool, cudaStream_t st, bool with_f32 = false) {
   D.n = A.nrows;
+  D.nnz = (int64_t)A.col.size();
   D.rp = pool.upload(A.rowptr, st);
   D.col = pool.upload(A.col, st);
   D.val = pool.upload(A.val, st);
@@ -574,6 +578,11 @@ struct hz_ctx {
   LevelDev lc;                // coarse ORAS level (or direct factors of E)
   int perturbed = 0;
   double setup_s = 0, factor_s = 0;
+  int device = -1;                 // the device hz_setup ran on
+  void* noalloc_scratch = nullptr; // device address of the allocation-free product's scratch
+  // per-column results of the last solve call (hz_column_stats)
+  std::vector<double> col_res;
+  std::vector<int> col_its;
   // workspaces (capacity s_cap columns)
   int s_cap = 0;
   DevPool work;
@@ -794,6 +803,41 @@ void spmm_A(hz_ctx* c, const double2* X, double2* Y, const double2* B, int s, in
   c->prof.end(id, c->st, fl, by);
 }
 
+// Algorithmic cost of the coarse phase of one application of M^{-1}: r_H =
+// Z^T v, the coarse solve (inner GMRES steps on E with coarse ORAS, or the
+// direct factors of E) and q = Z y_H. Bytes: the compulsory traffic of each
+// step (matrix and factor entries with their indices, the blocks read and
+// written); flops: complex multiply-add = 8 (real-by-complex = 4).
+void coarse_cost(const hz_ctx* c, int s, bool f32_input, double& flops, double& bytes) {
+  const LevelDev& L = c->lc;
+  const double es = L.mf.fp32 ? 8.0 : 16.0;         // block entry
+  const double vs = L.mf.fp32 ? 4.0 : 8.0;          // real matrix value
+  const double n = (double)c->space.n, nh = (double)c->cspace.n, sub = (double)L.sub_rows;
+  const double nz = (double)c->Z.nnz;
+  const double lf = (double)L.info.factor_entries;
+  // Z^T v and Z y (+ the FP64 -> FP32 cast of v in the FP32 coarse form)
+  bytes = 2.0 * (nz * (vs + 4.0) + 8.0 * (n + 1.0)) + 2.0 * es * s * (n + nh);
+  flops = 2.0 * 4.0 * nz * s;
+  if (f32_input) bytes += 24.0 * n * s;
+  // one application of coarse ORAS (gather, front sweeps, owner scatter)
+  const double oras_b = 4.0 * sub + 2.0 * es * sub * s + es * 2.0 * lf + 2.0 * es * sub * s + 4.0 * nh + 2.0 * es * nh * s;
+  const double oras_f = 8.0 * s * 2.0 * lf;
+  if (c->opt.coarse_mode == HZ_COARSE_DIRECT) {
+    bytes += oras_b;
+    flops += oras_f;
+    return;
+  }
+  const double nzE = (double)(c->E.nnz_re + c->E.nnz_im);
+  const int m = std::max(1, c->opt.coarse_inner_its);
+  bytes += 3.0 * es * nh * s;  // Krylov start: norm, scale
+  for (int j = 0; j < m; ++j) {
+    bytes += oras_b + nzE * (vs + 4.0) + 8.0 * (nh + 1.0) + 2.0 * es * nh * s + es * nh * s * (4.0 * (j + 1) + 6.0);
+    flops += oras_f + 4.0 * nzE * s + 2.0 * 2.0 * 8.0 * nh * (j + 1) * s;
+  }
+  bytes += es * nh * s * (m + 2.0);  // X += Zk y
+  flops += 8.0 * nh * s * m;
+}
+
 // Zout = M^{-1} V (Eq. 2lvl; Eq. oras without a coarse level)
 void apply_prec(hz_ctx* c, const double2* V, double2* Zout, int s) {
   cudaStream_t st = c->st;
@@ -811,7 +855,11 @@ void apply_prec(hz_ctx* c, const double2* V, double2* Zout, int s) {
     run_graph(c->opt.use_graphs ? &c->g_coarse : nullptr, s, st,
               [&]() { coarse_solve(c, nullptr, nullptr, s); });                         // y_H ~ E^{-1} r_H
     spmm_real_f32(c->Z.n, c->Z.rp, c->Z.col, c->Z.val_f, c->yH32, c->q32, s, st);      // q = Z y_H
-    c->prof.end(id, st, 0.0, 0.0);
+    if (id >= 0) {
+      double cf, cb;
+      coarse_cost(c, s, true, cf, cb);
+      c->prof.end(id, st, cf, cb);
+    }
     int ip = c->prof.begin(PH_PSPMM, st);
     spmm_split_f32(c->A, c->q32, c->t32, s, st, c->v32);                               // t = v - A q
     c->prof.end(ip, st, 4.0 * (c->A.nnz_re + c->A.nnz_im) * s,
@@ -834,7 +882,11 @@ void apply_prec(hz_ctx* c, const double2* V, double2* Zout, int s) {
   run_graph(c->opt.use_graphs ? &c->g_coarse : nullptr, s, st,
             [&]() { coarse_solve(c, c->rH, c->yH, s); });                 // y_H ~ E^{-1} r_H
   spmm_real(c->Z.n, c->Z.rp, c->Z.col, c->Z.val, c->yH, c->Q, s, st);    // q = Z y_H
-  c->prof.end(id, st, 0.0, 0.0);
+  if (id >= 0) {
+    double cf, cb;
+    coarse_cost(c, s, false, cf, cb);
+    c->prof.end(id, st, cf, cb);
+  }
   spmm_A(c, c->Q, c->T, V, s, 1);                                         // t = v - A q
   apply_oras(c->lf, c->T, Zout, c->Q, c->Xsub, s, st, &c->prof, gf);      // z = M1^{-1} t + q
 }
@@ -901,9 +953,12 @@ int fgmres(hz_ctx* c, int s, hz_stats* stats) {
   int its = 0, restarts = 0;
   bool all_conv = false;
   double maxrel = 0.0;
+  std::vector<int> col_its(s, 0), kc(s);
   while (true) {
     its += fgmres_cycle(c, s, c->opt.maxit - its);
-    true_residual(c, s);
+    CK(cudaMemcpyAsync(kc.data(), K.kc, s * sizeof(int), cudaMemcpyDeviceToHost, st));
+    true_residual(c, s);  // synchronises the stream
+    for (int q = 0; q < s; ++q) col_its[q] += kc[q];
     all_conv = true;
     maxrel = 0.0;
     for (int q = 0; q < s; ++q) {
@@ -916,12 +971,10 @@ int fgmres(hz_ctx* c, int s, hz_stats* stats) {
     if (all_conv || its >= c->opt.maxit) break;
     ++restarts;
   }
-  for (DevMF* mf : {&c->lf.mf, &c->lc.mf})
-    if (mf->tc_err) {  // a tensor-core tile gave up waiting on one of its barriers
-      int e = 0;
-      CK(cudaMemcpy(&e, mf->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
-      if (e) throw HzError{HZ_EINTERNAL, "tensor-core sweep tile timed out on a barrier"};
-    }
+  for (int q = 0; q < s; ++q) {
+    c->col_res.push_back(bn[q] > 0 ? c->h_res[q] / bn[q] : 0.0);
+    c->col_its.push_back(col_its[q]);
+  }
   if (stats) {
     stats->iterations = its;
     stats->restarts = restarts;
@@ -930,6 +983,24 @@ int fgmres(hz_ctx* c, int s, hz_stats* stats) {
     stats->max_rel_residual = maxrel;
   }
   return all_conv ? HZ_OK : HZ_ENOTCONV;
+}
+
+// Read and clear the device flags that the tensor-core sweep tiles set when
+// they give up waiting on one of their barriers; called after every entry
+// point that ran the sweeps, so that a timeout is reported by the call in
+// which it happened and does not fail later calls.
+void check_sweep_flags(hz_ctx* c) {
+  for (DevMF* mf : {&c->lf.mf, &c->lc.mf})
+    if (mf->tc_err) {
+      int e = 0;
+      CK(cudaMemcpyAsync(&e, mf->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      if (e) {
+        CK(cudaMemsetAsync(mf->tc_err, 0, sizeof(int), c->st));
+        CK(cudaStreamSynchronize(c->st));
+        throw HzError{HZ_EINTERNAL, "tensor-core sweep tile timed out on a barrier"};
+      }
+    }
 }
 
 int fail(int code, const std::string& msg) {
@@ -957,6 +1028,43 @@ void check_launch() {
   if (e != cudaSuccess) throw CudaFail{e, "kernel launch"};
 }
 
+// debug_bounds: one device pass over the index maps of the hot path
+void check_bounds(hz_ctx* c) {
+  cudaStream_t st = c->st;
+  int* d_err = c->pool.alloc<int>(1);
+  const int big = 0x7fffffff;
+  CK(cudaMemcpyAsync(d_err, &big, sizeof(int), cudaMemcpyHostToDevice, st));
+  std::vector<std::string> names;
+  auto chk = [&](const char* nm, const void* a, int64_t count, int stride, int64_t lo, int64_t hi) {
+    check_index_range((const int*)a, count, stride, lo, hi, d_err, (int)names.size(), st);
+    names.push_back(nm);
+  };
+  auto chk_csr = [&](const char* nm, const int32_t* col, int64_t nnz, int64_t ncols) { chk(nm, col, nnz, 1, 0, ncols); };
+  chk_csr("A columns (real part)", c->A.col_re, c->A.nnz_re, c->A.ncols);
+  chk_csr("A columns (imaginary part)", c->A.col_im, c->A.nnz_im, c->A.ncols);
+  for (int lev = 0; lev < (c->has_coarse ? 2 : 1); ++lev) {
+    LevelDev& L = lev ? c->lc : c->lf;
+    const DevMF& mf = L.mf;
+    chk(lev ? "coarse R_i map" : "fine R_i map", mf.gidx, mf.nsub_rows, 1, 0, L.n);
+    chk(lev ? "coarse owner map" : "fine owner map", mf.own, L.n, 1, 0, mf.nsub_rows);
+    chk(lev ? "coarse front rows" : "fine front rows", mf.rows, mf.rows_total, 1, 0, mf.nsub_rows);
+    chk(lev ? "coarse extend-add sources" : "fine extend-add sources", mf.cidx, mf.cidx_n, 1, 0, mf.rows_total);
+    chk(lev ? "coarse level list" : "fine level list", mf.level_list, mf.nfronts, 1, 0, mf.nfronts);
+    chk(lev ? "coarse forward tiles" : "fine forward tiles", mf.ftiles, mf.ftiles_n, 4, 0, mf.nfronts);
+    chk(lev ? "coarse backward tiles" : "fine backward tiles", mf.btiles, mf.btiles_n, 4, 0, mf.nfronts);
+  }
+  if (c->has_coarse) {
+    chk_csr("E columns", c->E.col_re, c->E.nnz_re, c->E.ncols);
+    chk_csr("Z columns", c->Z.col, c->Z.nnz, c->cspace.n);
+    chk_csr("Z^T columns", c->ZT.col, c->ZT.nnz, c->space.n);
+  }
+  check_launch();
+  int h = big;
+  CK(cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h != big) throw HzError{HZ_EINTERNAL, "debug_bounds: index out of range in " + names[h]};
+}
+
 // order the library stream after the work already queued on the caller's stream
 void join_user(hz_ctx* c) {
   CK(cudaEventRecord(c->ev_join, c->user_st));
@@ -972,6 +1080,11 @@ const DevSplitCsr* ctx_matrix(const hz_ctx* c, int64_t* n) {
   return &c->A;
 }
 void set_last_error(const char* msg) { g_last_error = msg; }
+void ctx_noalloc(const hz_ctx* c, int* device, void** scratch) {
+  *device = c->device;
+  *scratch = c->noalloc_scratch;
+}
+cudaError_t noalloc_scratch_address(void** out);  // noalloc.cu
 }  // namespace hz
 
 extern "C" {
@@ -990,6 +1103,9 @@ int hz_default_options(hz_options* o) {
   o->verbose = 0;
   o->use_graphs = 1;
   o->tensor_cores = 0;
+  o->overlap = 1;
+  o->coarse_fp32 = 0;
+  o->debug_bounds = 0;
   return HZ_OK;
 }
 
@@ -1013,6 +1129,7 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
     if (o.coarse_mode < 0 || o.coarse_mode > 2) throw HzError{HZ_EINVAL, "bad coarse_mode"};
     if (o.coarse_mode != HZ_COARSE_NONE && !coarse) throw HzError{HZ_EINVAL, "coarse mesh required"};
     if (o.coarse_mode == HZ_COARSE_GMRES && o.coarse_inner_its < 1) throw HzError{HZ_EINVAL, "coarse_inner_its < 1"};
+    if (o.overlap < 1 || o.overlap > 16) throw HzError{HZ_EINVAL, "overlap must be in [1, 16]"};
     mesh_from_abi(fine, c->fine);
     mesh_build_adjacency(c->fine);
     const int64_t ne = c->fine.ne;
@@ -1033,6 +1150,7 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
     c->omega = omega;
     c->mvals = mvals;
     c->user_st = (cudaStream_t)stream;
+    CK(cudaGetDevice(&c->device));
     CK(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     join_user(c.get());
@@ -1041,7 +1159,7 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
     c->A_host = assemble_global(c->fine, c->space, mvals, omega);
     const bool mixed = o.precision == HZ_PREC_MIXED;
     upload_split(c->A_host, c->A, c->pool, c->st, mixed);
-    std::vector<Subdomain> subs = build_subdomains(c->fine, c->space, part, nparts, mvals, omega);
+    std::vector<Subdomain> subs = build_subdomains(c->fine, c->space, part, nparts, mvals, omega, o.overlap);
     const bool tc = mixed && o.tensor_cores != 0;
     build_level(c->space, subs, o.leaf_size, mixed, tc, c->lf, c->pool, c->st);
     subs.clear();
@@ -1050,14 +1168,17 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
       mesh_from_abi(coarse, c->coarse);
       CoarseSpace C = build_coarse(c->fine, c->space, mvals, part, omega, c->coarse);
       c->cspace = C.space;
-      upload_split(C.E, c->E, c->pool, c->st, mixed && o.coarse_mode == HZ_COARSE_GMRES);
-      upload_real(C.Z, c->Z, c->pool, c->st, mixed);
-      upload_real(C.ZT, c->ZT, c->pool, c->st, mixed);
+      // coarse level in FP64 unless the mixed form asks for an FP32 coarse level
+      const bool cf32 = mixed && o.coarse_fp32 != 0;
+      upload_split(C.E, c->E, c->pool, c->st, cf32 && o.coarse_mode == HZ_COARSE_GMRES);
+      upload_real(C.Z, c->Z, c->pool, c->st, cf32);
+      upload_real(C.ZT, c->ZT, c->pool, c->st, cf32);
       if (o.coarse_mode == HZ_COARSE_GMRES) {
-        std::vector<Subdomain> csubs = build_subdomains(c->coarse, c->cspace, C.part, nparts, C.mvals, omega);
-        build_level(c->cspace, csubs, o.leaf_size, mixed, tc, c->lc, c->pool, c->st);
+        std::vector<Subdomain> csubs =
+            build_subdomains(c->coarse, c->cspace, C.part, nparts, C.mvals, omega, o.overlap);
+        build_level(c->cspace, csubs, o.leaf_size, cf32, tc, c->lc, c->pool, c->st);
       } else {
-        build_direct(c->cspace, C.E, o.leaf_size, mixed, tc, c->lc, c->pool, c->st);
+        build_direct(c->cspace, C.E, o.leaf_size, cf32, tc, c->lc, c->pool, c->st);
       }
     }
     CK(cudaStreamSynchronize(c->st));
@@ -1082,6 +1203,11 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
     }
     c->perturbed = pf + pcnt;
     if (o.pivot_tau == 0.0 && c->perturbed) throw HzError{HZ_ESINGULAR, "zero pivot in a local factorisation"};
+    if (o.debug_bounds) {
+      check_bounds(c.get());
+    }
+    // address of the allocation-free product's scratch on this device (loads it here)
+    hz::noalloc_scratch_address(&c->noalloc_scratch);
     c->setup_s = now_s() - t0;
     if (o.verbose)
       fprintf(stderr, "[hz] setup n=%lld nnz=%lld fronts=%d levels=%d max_front=%d factor %.3fs total %.3fs\n",
@@ -1133,6 +1259,17 @@ int hz_get_info(const hz_ctx* c, hz_info* info) {
   info->perturbed_pivots = c->perturbed;
   info->device_bytes = c->pool.bytes + c->work.bytes;
   info->kernel_launches = g_kernel_launches.load();
+  return HZ_OK;
+}
+
+int hz_column_stats(const hz_ctx* c, double* rel_residual, int32_t* iterations, int32_t cap, int32_t* ncols) {
+  if (!c || !ncols || cap < 0) return fail(HZ_EINVAL, "bad argument");
+  const int nc = (int)c->col_res.size();
+  *ncols = nc;
+  for (int q = 0; q < std::min<int>(nc, cap); ++q) {
+    if (rel_residual) rel_residual[q] = c->col_res[q];
+    if (iterations) iterations[q] = c->col_its[q];
+  }
   return HZ_OK;
 }
 
@@ -1224,6 +1361,7 @@ int hz_apply_prec(hz_ctx* c, const double* X, double* Y, int32_t s, int32_t on_d
     apply_prec(c, c->B, c->R, s);
     check_launch();
     store_block(c, c->R, Y, s, on_device);
+    check_sweep_flags(c);
     return HZ_OK;
   });
 }
@@ -1235,6 +1373,8 @@ int hz_solve_rhs(hz_ctx* c, const double* F, int32_t ns, int32_t F_on_device, do
     join_user(c);
     const double t0 = now_s();
     const int64_t n = c->space.n;
+    c->col_res.clear();
+    c->col_its.clear();
     int rc = HZ_OK;
     hz_stats agg;
     std::memset(&agg, 0, sizeof(agg));
@@ -1257,6 +1397,8 @@ int hz_solve_rhs(hz_ctx* c, const double* F, int32_t ns, int32_t F_on_device, do
     agg.solve_seconds = now_s() - t0;
     agg.setup_seconds = c->setup_s;
     agg.factor_seconds = c->factor_s;
+    agg.perturbed_pivots = c->perturbed;
+    check_sweep_flags(c);
     if (stats) *stats = agg;
     if (rc != HZ_OK) g_last_error = "FGMRES reached maxit before rtol";
     return rc;
@@ -1270,6 +1412,8 @@ int hz_solve(hz_ctx* c, const double* src_xyz, const double* src_amp, int32_t ns
     join_user(c);
     const double t0 = now_s();
     const int64_t n = c->space.n;
+    c->col_res.clear();
+    c->col_its.clear();
     std::vector<int64_t> elem(ns);
     std::vector<double> lam(4 * (size_t)ns);
     locate_points(c->fine, src_xyz, ns, elem.data(), lam.data());
@@ -1323,6 +1467,8 @@ int hz_solve(hz_ctx* c, const double* src_xyz, const double* src_amp, int32_t ns
     agg.solve_seconds = now_s() - t0;
     agg.setup_seconds = c->setup_s;
     agg.factor_seconds = c->factor_s;
+    agg.perturbed_pivots = c->perturbed;
+    check_sweep_flags(c);
     if (stats) *stats = agg;
     if (rc != HZ_OK) g_last_error = "FGMRES reached maxit before rtol";
     return rc;
@@ -1423,6 +1569,7 @@ struct hz_server {
   std::vector<int> slot_its;
   std::vector<double> slot_bn;
   std::map<int64_t, Req> reqs;
+  std::deque<int64_t> finished;  // finished request ids not yet returned by hz_server_step
   // the slots' right-hand sides, iterates and residuals persist across
   // steps: the server owns them and lends them to the context for each step
   double2 *B = nullptr, *X = nullptr, *R = nullptr, *d_col = nullptr;
@@ -1500,8 +1647,15 @@ extern "C" int hz_server_submit(hz_server* v, int64_t id, const double* src_xyz,
 }
 
 extern "C" int hz_server_step(hz_server* v, int64_t* done_ids, int32_t cap, int32_t* ndone) {
-  if (!v || !ndone || (cap > 0 && !done_ids)) return fail(HZ_EINVAL, "bad argument");
+  if (!v || !ndone || cap < 0 || (cap > 0 && !done_ids)) return fail(HZ_EINVAL, "bad argument");
   *ndone = 0;
+  // hand out up to cap finished ids (oldest first); the rest wait for the next step
+  auto drain = [&]() {
+    while (*ndone < cap && !v->finished.empty()) {
+      done_ids[(*ndone)++] = v->finished.front();
+      v->finished.pop_front();
+    }
+  };
   return guarded([&]() -> int {
     hz_ctx* c = v->c;
     cudaStream_t st = c->st;
@@ -1524,7 +1678,10 @@ extern "C" int hz_server_step(hz_server* v, int64_t* done_ids, int32_t cap, int3
     }
     int active = 0;
     for (int q = 0; q < s; ++q) active += v->slot[q].req >= 0;
-    if (active == 0) return HZ_OK;
+    if (active == 0) {
+      drain();
+      return HZ_OK;
+    }
     if (!idx.empty()) {
       upload_sources(c, idx, val);
       scatter_point_sources(c->B, n, s, c->d_srcidx, c->d_srcval, (int)idx.size(), st);
@@ -1568,11 +1725,13 @@ extern "C" int hz_server_step(hz_server* v, int64_t* done_ids, int32_t cap, int3
       col_zero(c->B, n, s, q, st);
       col_zero(c->X, n, s, q, st);
       col_zero(c->R, n, s, q, st);
-      if (--r.remaining == 0 && *ndone < cap) done_ids[(*ndone)++] = v->slot[q].req;
+      if (--r.remaining == 0) v->finished.push_back(v->slot[q].req);
       v->slot[q].req = -1;
     }
     check_launch();
     CK(cudaStreamSynchronize(st));
+    check_sweep_flags(c);
+    drain();
     return HZ_OK;
   });
 }
@@ -1682,6 +1841,10 @@ extern "C" int hz_fwi_gradient(hz_ctx* c, const double* src_xyz, const double* s
     join_user(c);
     const double t0 = now_s();
     const int64_t n = c->space.n, ne = c->fine.ne;
+    c->col_res.clear();
+    c->col_its.clear();
+    std::vector<double> fwd_res, adj_res;
+    std::vector<int> fwd_its, adj_its;
     cudaStream_t st = c->st;
     // receivers: P as [nr][20] (dof, weight) and its transpose in CSR over the touched dofs
     std::vector<int> pidx((size_t)nr * NLOC);
@@ -1748,6 +1911,9 @@ extern "C" int hz_fwi_gradient(hz_ctx* c, const double* src_xyz, const double* s
       check_launch();
       if (r != HZ_OK) rc = r;
       add_stats(a);
+      // fgmres appended this block's columns: keep forward and adjoint columns apart
+      fwd_res.insert(fwd_res.end(), c->col_res.end() - s, c->col_res.end());
+      fwd_its.insert(fwd_its.end(), c->col_its.end() - s, c->col_its.end());
       CK(cudaMemcpyAsync(d_u, c->X, (size_t)n * s * sizeof(double2), cudaMemcpyDeviceToDevice, st));
       // residual at the receivers and misfit
       if (d_obs)
@@ -1772,6 +1938,8 @@ extern "C" int hz_fwi_gradient(hz_ctx* c, const double* src_xyz, const double* s
       check_launch();
       if (r != HZ_OK) rc = r;
       add_stats(a);
+      adj_res.insert(adj_res.end(), c->col_res.end() - s, c->col_res.end());
+      adj_its.insert(adj_its.end(), c->col_its.end() - s, c->col_its.end());
       // g_e -= Re sum_s lambda_e^T dA/dm_e u_e
       fwi_gradient(ne, s, c->d_fwi_l2g, c->d_fwi_vol, c->d_fwi_farea, c->d_fwi_m, c->omega, d_u, c->X, d_g, st);
       check_launch();
@@ -1781,10 +1949,16 @@ extern "C" int hz_fwi_gradient(hz_ctx* c, const double* src_xyz, const double* s
     CK(cudaMemcpyAsync(&h_chi, d_chi, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (chi) *chi = h_chi;
+    c->col_res = fwd_res;
+    c->col_res.insert(c->col_res.end(), adj_res.begin(), adj_res.end());
+    c->col_its = fwd_its;
+    c->col_its.insert(c->col_its.end(), adj_its.begin(), adj_its.end());
     agg.ncols = 2 * ns;
     agg.solve_seconds = now_s() - t0;
     agg.setup_seconds = c->setup_s;
     agg.factor_seconds = c->factor_s;
+    agg.perturbed_pivots = c->perturbed;
+    check_sweep_flags(c);
     if (stats) *stats = agg;
     if (rc != HZ_OK) g_last_error = "FGMRES reached maxit before rtol";
     return rc;

@@ -212,6 +212,20 @@ void transpose_from_rows(const double2* B, double2* F, int64_t n, int s, cudaStr
   if (n * s) { k_from_rows<<<grid_for(n * s, 256), 256, 0, st>>>(B, F, n, s); count_launch(); }
 }
 
+// debug_bounds: every entry a[i * stride] must lie in [lo, hi); the smallest
+// failing check id is kept in *err (initialised to INT_MAX by the caller)
+__global__ void k_check_range(const int* __restrict__ a, int64_t count, int stride, int64_t lo, int64_t hi,
+                              int* __restrict__ err, int id) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int64_t v = a[i * stride];
+  if (v < lo || v >= hi) atomicMin(err, id);
+}
+void check_index_range(const int* a, int64_t count, int stride, int64_t lo, int64_t hi, int* err, int id,
+                       cudaStream_t st) {
+  if (count > 0 && a) { k_check_range<<<grid_for(count, 256), 256, 0, st>>>(a, count, stride, lo, hi, err, id); count_launch(); }
+}
+
 __global__ void k_copy(const double2* __restrict__ X, double2* __restrict__ Y, int64_t count) {
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g < count) Y[g] = X[g];

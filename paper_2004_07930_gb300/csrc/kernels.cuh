@@ -51,6 +51,8 @@ struct DevMF {
   int* row_local = nullptr;     // [rows_total] position inside its front
   int64_t* cptr = nullptr;      // [rows_total+1] extend-add sources of each front row
   int* cidx = nullptr;          // child update rows, in child order
+  int64_t cidx_n = 0;           // entries of cidx
+  int64_t ftiles_n = 0, btiles_n = 0;  // tiles of each sweep (all levels)
   void* P = nullptr;            // partial tile results [max_slots][128][s_cap]
   int* k = nullptr;             // pivots per front
   int* f = nullptr;             // front order k + m
@@ -174,6 +176,9 @@ void scatter_point_sources(double2* B, int64_t n, int s, const int* idx, const d
 void transpose_to_rows(const double2* F, double2* B, int64_t n, int s, cudaStream_t st);    // [s][n] -> [n][s]
 void transpose_from_rows(const double2* B, double2* F, int64_t n, int s, cudaStream_t st);  // [n][s] -> [s][n]
 void cast_copy(const double2* X, double2* Y, int64_t count, cudaStream_t st);
+// debug_bounds: atomicMin(err, id) if some a[i * stride], i < count, lies outside [lo, hi)
+void check_index_range(const int* a, int64_t count, int stride, int64_t lo, int64_t hi, int* err, int id,
+                       cudaStream_t st);
 // one column c of an [n][s] block
 void col_zero(double2* X, int64_t n, int s, int c, cudaStream_t st);
 void col_copy(const double2* X, double2* Y, int64_t n, int s, int c, cudaStream_t st);

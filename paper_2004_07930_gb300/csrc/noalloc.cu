@@ -11,52 +11,40 @@
 // of hz_apply_A (layout change, split real/imaginary SpMM, layout change).
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "../../include/hz.h"
 #include "kernels.cuh"
 
 namespace hz {
-const DevSplitCsr* ctx_matrix(const hz_ctx* c, int64_t* n);  // hz_api.cu
-void set_last_error(const char* msg);                        // hz_api.cu
+const DevSplitCsr* ctx_matrix(const hz_ctx* c, int64_t* n);    // hz_api.cu
+void ctx_noalloc(const hz_ctx* c, int* device, void** scratch);  // hz_api.cu
+void set_last_error(const char* msg);                          // hz_api.cu
 }  // namespace hz
 
 namespace {
 
 // Scratch of the allocation-free product: two blocks of HZ_NOALLOC_MAX_ENTRIES
-// complex values (32 MiB in total), held by every GPU that loads the library
-// until the process exits. All calls share it; every call overwrites the
-// entries it reads, so nothing has to start at zero.
+// complex values (32 MiB in total). All calls share it; every call
+// overwrites the entries it reads, so nothing has to start at zero.
 constexpr int64_t kMaxEntries = HZ_NOALLOC_MAX_ENTRIES;
 static __device__ __align__(256) double2 hz_noalloc_scratch[2 * kMaxEntries];
 
-// Host code cannot use the symbol as an address: its device address is
-// looked up once per device (with that device current) and cached.
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double2* g_scratch[kMaxDevices] = {};
-
-int scratch_for_current_device(double2** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    cudaGetLastError();
-    return HZ_ECUDA;
-  }
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, hz_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return HZ_ECUDA;
-    }
-    g_scratch[dev] = (double2*)p;
-  }
-  *out = g_scratch[dev];
-  return HZ_OK;
-}
-
 }  // namespace
+
+namespace hz {
+// Device address of the scratch array on the current device. Host code
+// cannot use the symbol itself as an address; hz_setup calls this once with
+// the context's device current (which loads the array there) and keeps the
+// result in the context.
+cudaError_t noalloc_scratch_address(void** out) {
+  *out = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(out, hz_noalloc_scratch);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *out = nullptr;
+  }
+  return e;
+}
+}  // namespace hz
 
 extern "C" int hz_apply_A_noalloc(hz_ctx* ctx, const double* X, double* Y, int32_t s, void* stream) {
   using namespace hz;
@@ -70,12 +58,24 @@ extern "C" int hz_apply_A_noalloc(hz_ctx* ctx, const double* X, double* Y, int32
     set_last_error("hz_apply_A_noalloc: n * s exceeds HZ_NOALLOC_MAX_ENTRIES");
     return HZ_EINVAL;
   }
-  double2* scratch = nullptr;
-  if (scratch_for_current_device(&scratch) != HZ_OK) {
-    set_last_error("hz_apply_A_noalloc: cudaGetSymbolAddress failed");
+  int ctx_dev = -1, cur = -1;
+  void* scr = nullptr;
+  ctx_noalloc(ctx, &ctx_dev, &scr);
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    set_last_error("hz_apply_A_noalloc: cudaGetDevice failed");
+    return HZ_ECUDA;
+  }
+  if (cur != ctx_dev) {
+    set_last_error("hz_apply_A_noalloc: the current device is not the context's device");
+    return HZ_EINVAL;
+  }
+  if (!scr) {
+    set_last_error("hz_apply_A_noalloc: the scratch array could not be looked up at setup");
     return HZ_ECUDA;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  double2* scratch = (double2*)scr;
   double2* B = scratch;                // [n][s] input rows
   double2* R = scratch + kMaxEntries;  // [n][s] product rows
   transpose_to_rows(reinterpret_cast<const double2*>(X), B, n, s, st);

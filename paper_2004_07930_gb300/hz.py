@@ -21,7 +21,7 @@ EXPORTS = ["hz_default_options", "hz_setup", "hz_ndof", "hz_dof_coords", "hz_get
            "hz_solve_rhs", "hz_apply_A", "hz_apply_prec", "hz_matrix_csr", "hz_free", "hz_strerror",
            "hz_last_error", "hz_profile_begin", "hz_profile_end", "hz_apply_A_noalloc", "hz_server_create",
            "hz_server_submit", "hz_server_step", "hz_server_fetch", "hz_server_pending", "hz_server_free",
-           "hz_receiver_operator", "hz_fwi_gradient"]
+           "hz_receiver_operator", "hz_fwi_gradient", "hz_column_stats"]
 HZ_NOALLOC_MAX_ENTRIES = 1048576  # complex entries per work block of hz_apply_A_noalloc (n * s)
 
 
@@ -34,13 +34,14 @@ class HzOptions(C.Structure):
     _fields_ = [("precision", C.c_int32), ("rtol", C.c_double), ("maxit", C.c_int32), ("restart", C.c_int32),
                 ("max_block", C.c_int32), ("coarse_mode", C.c_int32), ("coarse_inner_its", C.c_int32),
                 ("leaf_size", C.c_int32), ("pivot_tau", C.c_double), ("verbose", C.c_int32),
-                ("use_graphs", C.c_int32), ("tensor_cores", C.c_int32)]
+                ("use_graphs", C.c_int32), ("tensor_cores", C.c_int32), ("overlap", C.c_int32),
+                ("coarse_fp32", C.c_int32), ("debug_bounds", C.c_int32)]
 
 
 class HzStats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("restarts", C.c_int32), ("converged", C.c_int32),
                 ("ncols", C.c_int32), ("max_rel_residual", C.c_double), ("solve_seconds", C.c_double),
-                ("setup_seconds", C.c_double), ("factor_seconds", C.c_double)]
+                ("setup_seconds", C.c_double), ("factor_seconds", C.c_double), ("perturbed_pivots", C.c_int32)]
 
     def asdict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -101,6 +102,7 @@ def load():
     lib.hz_server_free.restype = None
     lib.hz_receiver_operator.argtypes = [P, P, C.c_int32, P, P]
     lib.hz_fwi_gradient.argtypes = [P, P, P, C.c_int32, P, C.c_int32, P, P, P, P, C.POINTER(HzStats)]
+    lib.hz_column_stats.argtypes = [P, P, P, C.c_int32, C.POINTER(C.c_int32)]
     lib.hz_profile_begin.argtypes = [P]
     lib.hz_profile_end.argtypes = [P, C.POINTER(HzPhaseTime), C.c_int32, C.POINTER(C.c_int32)]
     lib.hz_free.argtypes = [P]
@@ -224,6 +226,16 @@ class Solver:
         _check(self._lib.hz_matrix_csr(self._ctx, rp.ctypes.data, col.ctypes.data, val.ctypes.data))
         return sp.csr_matrix((val, col, rp), shape=(self.n, self.n))
 
+    def column_stats(self):
+        """(rel_residual [ncols], iterations [ncols]) of every column of the
+        last solve call, in source order (FWI: forward columns, then adjoint)."""
+        nc = C.c_int32()
+        _check(self._lib.hz_column_stats(self._ctx, None, None, 0, C.byref(nc)))
+        res = np.empty(nc.value, dtype=np.float64)
+        its = np.empty(nc.value, dtype=np.int32)
+        _check(self._lib.hz_column_stats(self._ctx, res.ctypes.data, its.ctypes.data, nc.value, C.byref(nc)))
+        return res, its
+
     def profile_begin(self):
         _check(self._lib.hz_profile_begin(self._ctx))
 
@@ -335,11 +347,12 @@ class Server:
             np.ascontiguousarray(src_amp, dtype=np.complex128).reshape(-1)
         _check(self._lib.hz_server_submit(self._h, int(request_id), src.ctypes.data, amp.ctypes.data, len(src)))
 
-    def step(self):
-        """One restart cycle; returns the ids of the requests that finished."""
-        done = np.empty(4096, dtype=np.int64)
+    def step(self, cap=4096):
+        """One restart cycle; returns the ids of the requests that finished
+        (at most cap; the others come with the next steps)."""
+        done = np.empty(max(cap, 1), dtype=np.int64)
         nd = C.c_int32()
-        _check(self._lib.hz_server_step(self._h, done.ctypes.data, len(done), C.byref(nd)))
+        _check(self._lib.hz_server_step(self._h, done.ctypes.data, int(cap), C.byref(nd)))
         return done[: nd.value].tolist()
 
     def fetch(self, request_id, ns):

@@ -37,16 +37,17 @@ def test_default_options(lib):
     o = hz.default_options()
     assert o.rtol == 1e-6 and o.restart == 30 and o.max_block == 64 and o.coarse_inner_its == 10
     assert o.coarse_mode == hz.HZ_COARSE_GMRES
+    assert o.overlap == 1 and o.coarse_fp32 == 0 and o.debug_bounds == 0 and o.tensor_cores == 0
 
 
-def _setup_rc(prob, part=None, nparts=None, vel=None, freq=None):
+def _setup_rc(prob, part=None, nparts=None, vel=None, freq=None, **opts):
     import ctypes as C
 
     keep = []
     fm = hz._mesh(prob["fine"], keep)
     vel = np.ascontiguousarray(prob["velocity"] if vel is None else vel, dtype=np.float64)
     part = np.ascontiguousarray(prob["elem_part"] if part is None else part, dtype=np.int32)
-    opt = hz.default_options(coarse_mode=hz.HZ_COARSE_NONE)
+    opt = hz.default_options(coarse_mode=hz.HZ_COARSE_NONE, **opts)
     ctx = C.c_void_p()
     rc = hz.load().hz_setup(C.byref(fm), vel.ctypes.data, prob["freq"] if freq is None else freq,
                             part.ctypes.data, prob["nparts"] if nparts is None else nparts, None,
@@ -64,6 +65,8 @@ def test_setup_rejects_bad_inputs(lib):
     assert _setup_rc(p, part=empty, nparts=2) == hz.HZ_EINVAL      # subdomain 1 empty
     assert _setup_rc(p, vel=-p["velocity"]) == hz.HZ_EINVAL
     assert _setup_rc(p, freq=0.0) == hz.HZ_EINVAL
+    assert _setup_rc(p, overlap=0) == hz.HZ_EINVAL
+    assert _setup_rc(p, overlap=17) == hz.HZ_EINVAL
     assert "partition" in hz.load().hz_last_error().decode() or True
     assert lib.hz_strerror(hz.HZ_ENOTCONV).decode() == "not converged"
 
@@ -85,3 +88,5 @@ def test_calls_reject_null_context(lib):
     h = C.c_void_p()
     assert lib.hz_server_create(None, 4, C.byref(h)) == hz.HZ_EINVAL
     assert lib.hz_server_step(None, None, 0, C.byref(C.c_int32())) == hz.HZ_EINVAL
+    assert lib.hz_column_stats(None, None, None, 0, C.byref(C.c_int32())) == hz.HZ_EINVAL
+    assert lib.hz_apply_A_noalloc(None, None, None, 1, None) == hz.HZ_EINVAL

@@ -4,7 +4,8 @@ Inputs are seeded (workloads module); expected values come from the oracle
 (SciPy SuperLU and the exact two-level operator). Tolerances: the products
 and preconditioner applications are exact algorithms, so they agree to a few
 hundred units of rounding relative to the local conditioning (1e-9); the
-wavefields must agree to relative L2 <= 1e-6 (FP64 form).
+wavefields must agree to relative L2 <= 1e-6 (FP64 form) at GMRES rtol 1e-6
+and <= 1e-5 in the mixed form.
 """
 import numpy as np
 import pytest
@@ -67,7 +68,7 @@ def test_device_buffers_equal_host_buffers(cube):
         np.testing.assert_array_equal(Yh, Yd)
 
 
-@pytest.mark.parametrize("rtol,bound", [(1e-10, 1e-8), (1e-8, 1e-6), (1e-6, 1e-4)])
+@pytest.mark.parametrize("rtol,bound", [(1e-10, 1e-8), (1e-8, 1e-7), (1e-6, 1e-6)])
 def test_cube_wavefield_matches_oracle(cube, rtol, bound):
     p, T = cube
     space, A, F = oa.system(p["fine"], p["velocity"], p["freq"], p["src_xyz"])
