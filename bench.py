@@ -114,9 +114,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the FP64 form")
     ap.add_argument("--fp64-warmup", type=int, default=1, help="warm-up steps of the FP64 form")
-    ap.add_argument("--variants", default="one_level,coarse_fp32",
+    ap.add_argument("--variants", default="one_level,coarse_fp32,paper_resolution",
                     help="extra variants of the headline form: one_level (one-level ORAS; also runs the short "
-                         "serving stream), coarse_fp32 (mixed form with the coarse level in complex FP32)")
+                         "serving stream), coarse_fp32 (mixed form with the coarse level in complex FP32), "
+                         "paper_resolution (two- and one-level at 1.3 Hz on the same mesh: 5 P3 cells per "
+                         "local wavelength as in the paper, coarse mesh at 2.5)")
     ap.add_argument("--maxit", type=int, default=500, help="FGMRES iteration cap (lower it only for profiling runs)")
     ap.add_argument("--coarse", choices=["gmres", "none", "direct"], default="gmres",
                     help="coarse level of the headline forms (the paper's: gmres, 10 inner steps)")
@@ -528,12 +530,21 @@ def main():
                                      coarse_mode=cm)
         if i == 0:
             clk = clocks.stop()
+    from paper_2004_07930_gb300 import workloads as wl
+
     variants = {}
     for v in [x for x in args.variants.split(",") if x]:
         if v == "one_level":
             variants["one_level_" + forms[0]] = measure_form(prob, forms[0], args.steps, args.warmup, stream, ws,
                                                              torch, hz, False, coarse_mode=hz.HZ_COARSE_NONE,
                                                              serve=(forms[0] == "mixed" and ws == 1))
+        elif v == "paper_resolution" and args.config == "overthrust5":
+            # the same mesh at the paper's resolution: 5 P3 cells per local minimum wavelength
+            # (Sec. "Numerical results"), i.e. 1.3 Hz on the 5 Hz grid; coarse mesh at 2.5 cells per wavelength
+            p2 = wl.overthrust_problem(1.3, nparts=64, seed=0, cells_per_wavelength=5.0)
+            for nm, c2 in (("two_level", cm), ("one_level", hz.HZ_COARSE_NONE)):
+                variants["paper_resolution_%s_%s" % (nm, forms[0])] = measure_form(
+                    p2, forms[0], args.steps, args.warmup, stream, ws, torch, hz, False, coarse_mode=c2)
         elif v == "coarse_fp32" and forms[0] == "mixed" and args.coarse != "none":
             variants["coarse_fp32_mixed"] = measure_form(prob, "mixed", args.steps, args.warmup, stream, ws, torch,
                                                          hz, False, coarse_mode=cm, coarse_fp32=1)

@@ -91,16 +91,24 @@ typedef struct hz_options {
   int32_t use_graphs;       /* 1 (default): replay the local-solve and coarse-solve launch sequences
                                as captured CUDA graphs; 0: launch them one by one */
   int32_t tensor_cores;     /* mixed form only. 1: front-sweep tiles of at least 32 rows and 32 reduction
-                               indices run on the tcgen05 tensor cores (factors rounded to TF32, FP32
-                               accumulation) for blocks of 9-64 columns; 0 (default): SIMT FP32 sweeps */
+                               indices run on the tcgen05 tensor cores for blocks of 9-16 columns, as a
+                               three-term TF32 split of the FP32 factors and inputs (hi*hi + hi*lo + lo*hi,
+                               FP32 accumulation in TMEM), which keeps FP32 accuracy; other tiles and
+                               block widths use the SIMT FP32 sweeps. 0: SIMT FP32 sweeps only */
   int32_t overlap;          /* element layers added around each subdomain, each layer = every element
                                sharing a vertex with the current set (1, the default; >= 1) */
-  int32_t coarse_fp32;      /* mixed form only. 0 (default): the coarse level (E, the coarse local factors,
-                               the inner coarse GMRES) is applied in FP64 as in the FP64 form; 1: the whole
-                               of M^{-1}, coarse level included, runs on complex FP32 blocks */
+  int32_t coarse_fp32;      /* mixed form only. 0 (default): E = Z^T A Z, Z, Z^T and the inner coarse GMRES
+                               run in FP64; the coarse fronts, factorised in FP64 like all fronts, are applied
+                               in complex FP32 like the fine ones. 1: the whole of M^{-1}, coarse level
+                               included, runs on complex FP32 blocks */
   int32_t debug_bounds;     /* 1: after the factorisation, one device pass checks every index map of the
                                hot path (restriction, ownership, front rows, extend-add sources, tiles)
                                against its bounds; a violation fails hz_setup with HZ_EINTERNAL. 0 (default) */
+  int32_t block_arnoldi;    /* 0 (default): one Krylov space per right-hand side (per-column CGS with a
+                               selective second pass). 1: block FGMRES for hz_solve / hz_solve_rhs /
+                               hz_fwi_gradient, one Krylov space shared by the block: block CGS2 and CholQR2
+                               as tall-skinny FP64 products, linearly dependent right-hand sides deflated;
+                               needs max_block <= 32. Servers keep one Krylov space per column */
 } hz_options;
 
 typedef struct hz_stats {
@@ -179,6 +187,15 @@ int hz_solve(hz_ctx* ctx, const double* src_xyz, const double* src_amp, int32_t 
  * columns of that call, which may exceed cap (only cap entries are written).
  * Errors: HZ_EINVAL. */
 int hz_column_stats(const hz_ctx* ctx, double* rel_residual, int32_t* iterations, int32_t cap, int32_t* ncols);
+
+/* Orthonormal basis of the last FGMRES restart cycle of the last solve
+ * call (diagnostics and tests): *nblocks basis blocks of *ncols columns,
+ * written to V [nblocks][ncols][n][2] (host, caller-owned, room for cap
+ * blocks; only min(cap, *nblocks) are written). With block_arnoldi = 1 the
+ * nblocks x ncols vectors are orthonormal together (deflated directions are
+ * zero vectors); otherwise column c of every block belongs to the Krylov
+ * space of right-hand side c alone. Errors: HZ_EINVAL (no solve yet), HZ_ECUDA. */
+int hz_krylov_basis(hz_ctx* ctx, double* V, int32_t cap, int32_t* nblocks, int32_t* ncols);
 
 /* Same for given right-hand sides F [ns][n][2] (host or device). */
 int hz_solve_rhs(hz_ctx* ctx, const double* F, int32_t ns, int32_t F_on_device, double* u, int32_t u_on_device,

@@ -388,7 +388,21 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
     mf.TC = pool.alloc<unsigned char>((size_t)std::max<int64_t>(tc_bytes, 16));
     mf.tc_err = pool.alloc<int>(1);
     CK(cudaMemsetAsync(mf.tc_err, 0, sizeof(int), st));
+    CK(cudaStreamCreateWithFlags(&mf.side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&mf.ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&mf.ev_join, cudaEventDisableTiming));
   }
+}
+
+void destroy_side(DevMF& mf) {
+  if (mf.side) {
+    cudaStreamSynchronize(mf.side);
+    cudaStreamDestroy(mf.side);
+  }
+  if (mf.ev_fork) cudaEventDestroy(mf.ev_fork);
+  if (mf.ev_join) cudaEventDestroy(mf.ev_join);
+  mf.side = nullptr;
+  mf.ev_fork = mf.ev_join = nullptr;
 }
 
 void upload_split(const CsrC& A, DevSplitCsr& D, DevPool& pool, cudaStream_t st, bool with_f32 = false) {
@@ -572,6 +586,7 @@ struct hz_ctx {
   DevSplitCsr A;
   LevelDev lf;                // fine ORAS level
   bool has_coarse = false;
+  bool coarse32 = false;      // mixed form with coarse_fp32: the whole of M^{-1} on FP32 blocks
   Space cspace;
   DevSplitCsr E;
   DevReal Z, ZT;
@@ -591,6 +606,7 @@ struct hz_ctx {
   float2 *rH32 = nullptr, *yH32 = nullptr;
   float2 *v32 = nullptr, *q32 = nullptr, *t32 = nullptr;  // FP32 preconditioner blocks (mixed form)
   DevKrylov Kout, Kin;
+  DevBlockKrylov Bk;          // block FGMRES (option block_arnoldi), on Kout's basis arrays
   double* bnorm = nullptr;
   double* rnorm = nullptr;
   double* h_res = nullptr;    // pinned host
@@ -665,6 +681,33 @@ void ensure_workspace(hz_ctx* c, int s) {
   c->lf.mf.P = p.alloc<char>((size_t)c->lf.mf.max_slots * MF_TILE_ROWS * s * ef);
   c->lf.mf.s_cap = s;
   alloc_krylov(c->Kout, n, s, c->opt.restart, p, false);
+  if (c->opt.block_arnoldi) {
+    DevBlockKrylov& B = c->Bk;
+    const int m = c->opt.restart;
+    B.m = m;
+    B.s = s;
+    B.n = n;
+    B.nblk = 304;
+    B.V = (double2*)c->Kout.V;
+    B.Zk = (double2*)c->Kout.Zk;
+    B.W = (double2*)c->Kout.W;
+    B.Hd = p.alloc<double2>((size_t)(m + 1) * s * m * s);
+    B.Gr = p.alloc<double2>((size_t)(m + 1) * s * s);
+    B.rc = p.alloc<double>((size_t)m * s * s);
+    B.rsn = p.alloc<double2>((size_t)m * s * s);
+    B.part = p.alloc<double2>((size_t)B.nblk * (m + 1) * s * s);
+    B.h1 = p.alloc<double2>((size_t)(m + 1) * s * s);
+    B.h2 = p.alloc<double2>((size_t)(m + 1) * s * s);
+    B.gram = p.alloc<double2>((size_t)s * s);
+    B.R = p.alloc<double2>((size_t)s * s);
+    B.Racc = p.alloc<double2>((size_t)s * s);
+    B.Y = p.alloc<double2>((size_t)s * m * s);
+    B.res = c->Kout.res;
+    B.tol = c->Kout.tol;
+    B.done = c->Kout.done;
+    B.kb = p.alloc<int>(1);
+    B.deflated = p.alloc<int>(1);
+  }
   if (c->has_coarse) {
     const int64_t nh = c->cspace.n;
     c->rH = p.alloc<double2>(nh * s);
@@ -675,10 +718,10 @@ void ensure_workspace(hz_ctx* c, int s) {
     c->lc.mf.P = p.alloc<char>((size_t)c->lc.mf.max_slots * MF_TILE_ROWS * s * ec);
     c->lc.mf.s_cap = s;
     if (c->opt.coarse_mode == HZ_COARSE_GMRES) {
-      alloc_krylov(c->Kin, nh, s, std::max(1, c->opt.coarse_inner_its), p, c->lc.mf.fp32 != 0);
+      alloc_krylov(c->Kin, nh, s, std::max(1, c->opt.coarse_inner_its), p, c->coarse32);
       CK(cudaMemsetAsync(c->Kin.tol, 0, s * sizeof(double), c->st));
     }
-    if (c->lc.mf.fp32) {
+    if (c->coarse32) {
       c->rH32 = p.alloc<float2>(nh * s);
       c->yH32 = p.alloc<float2>(nh * s);
       c->v32 = p.alloc<float2>(n * s);
@@ -810,8 +853,9 @@ void spmm_A(hz_ctx* c, const double2* X, double2* Y, const double2* B, int s, in
 // written); flops: complex multiply-add = 8 (real-by-complex = 4).
 void coarse_cost(const hz_ctx* c, int s, bool f32_input, double& flops, double& bytes) {
   const LevelDev& L = c->lc;
-  const double es = L.mf.fp32 ? 8.0 : 16.0;         // block entry
-  const double vs = L.mf.fp32 ? 4.0 : 8.0;          // real matrix value
+  const double ef = L.mf.fp32 ? 8.0 : 16.0;         // factor and sub-vector entry
+  const double es = c->coarse32 ? 8.0 : 16.0;       // block entry (Krylov, E and Z products)
+  const double vs = c->coarse32 ? 4.0 : 8.0;        // real matrix value
   const double n = (double)c->space.n, nh = (double)c->cspace.n, sub = (double)L.sub_rows;
   const double nz = (double)c->Z.nnz;
   const double lf = (double)L.info.factor_entries;
@@ -820,7 +864,7 @@ void coarse_cost(const hz_ctx* c, int s, bool f32_input, double& flops, double& 
   flops = 2.0 * 4.0 * nz * s;
   if (f32_input) bytes += 24.0 * n * s;
   // one application of coarse ORAS (gather, front sweeps, owner scatter)
-  const double oras_b = 4.0 * sub + 2.0 * es * sub * s + es * 2.0 * lf + 2.0 * es * sub * s + 4.0 * nh + 2.0 * es * nh * s;
+  const double oras_b = 4.0 * sub + (es + ef) * sub * s + ef * 2.0 * lf + 2.0 * ef * sub * s + 4.0 * nh + (ef + es) * nh * s;
   const double oras_f = 8.0 * s * 2.0 * lf;
   if (c->opt.coarse_mode == HZ_COARSE_DIRECT) {
     bytes += oras_b;
@@ -922,6 +966,38 @@ int fgmres_cycle(hz_ctx* c, int s, int max_its) {
   return its;
 }
 
+// One restart cycle of block FGMRES (option block_arnoldi): one Krylov space
+// for the whole block from the current residual c->R (which it overwrites),
+// at most max_its block steps, then X += Z Y. Every column stops together.
+int fgmres_cycle_block(hz_ctx* c, int s, int max_its) {
+  cudaStream_t st = c->st;
+  const int64_t n = c->space.n;
+  DevBlockKrylov& B = c->Bk;
+  B.s = s;
+  const int m = std::min(c->opt.restart, max_its);
+  const int64_t vs = n * s;
+  int id0 = c->prof.begin(PH_ARNOLDI, st);
+  block_krylov_start(B, c->R, st);
+  c->prof.end(id0, st, 2.0 * 12.0 * n * s * s, 2.0 * 16.0 * n * s * 4.0);
+  int its = 0;
+  for (int j = 0; j < m; ++j) {
+    apply_prec(c, B.V + j * vs, B.Zk + j * vs, s);
+    spmm_A(c, B.Zk + j * vs, B.W, nullptr, s, 0);
+    int id = c->prof.begin(PH_ARNOLDI, st);
+    block_krylov_arnoldi(B, j, st);
+    // two CGS passes (Gram blocks + update) over V_0..j, then CholQR2 (two Gram + triangular solves)
+    c->prof.end(id, st, 32.0 * n * s * s * (j + 1) + 24.0 * n * s * s, 16.0 * n * s * (4.0 * (j + 1) + 14.0));
+    ++its;
+    CK(cudaMemcpyAsync(c->h_done, B.done, s * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    bool alldone = true;
+    for (int q = 0; q < s; ++q) alldone &= c->h_done[q] != 0;
+    if (alldone) break;
+  }
+  block_krylov_update(B, c->X, st);
+  return its;
+}
+
 // True residual R = B - A X and its column norms (host, into c->h_res).
 void true_residual(hz_ctx* c, int s) {
   cudaStream_t st = c->st;
@@ -954,11 +1030,13 @@ int fgmres(hz_ctx* c, int s, hz_stats* stats) {
   bool all_conv = false;
   double maxrel = 0.0;
   std::vector<int> col_its(s, 0), kc(s);
+  const bool block = c->opt.block_arnoldi != 0;
   while (true) {
-    its += fgmres_cycle(c, s, c->opt.maxit - its);
-    CK(cudaMemcpyAsync(kc.data(), K.kc, s * sizeof(int), cudaMemcpyDeviceToHost, st));
+    const int done_its = block ? fgmres_cycle_block(c, s, c->opt.maxit - its) : fgmres_cycle(c, s, c->opt.maxit - its);
+    its += done_its;
+    if (!block) CK(cudaMemcpyAsync(kc.data(), K.kc, s * sizeof(int), cudaMemcpyDeviceToHost, st));
     true_residual(c, s);  // synchronises the stream
-    for (int q = 0; q < s; ++q) col_its[q] += kc[q];
+    for (int q = 0; q < s; ++q) col_its[q] += block ? done_its : kc[q];
     all_conv = true;
     maxrel = 0.0;
     for (int q = 0; q < s; ++q) {
@@ -1106,6 +1184,7 @@ int hz_default_options(hz_options* o) {
   o->overlap = 1;
   o->coarse_fp32 = 0;
   o->debug_bounds = 0;
+  o->block_arnoldi = 0;
   return HZ_OK;
 }
 
@@ -1130,6 +1209,8 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
     if (o.coarse_mode != HZ_COARSE_NONE && !coarse) throw HzError{HZ_EINVAL, "coarse mesh required"};
     if (o.coarse_mode == HZ_COARSE_GMRES && o.coarse_inner_its < 1) throw HzError{HZ_EINVAL, "coarse_inner_its < 1"};
     if (o.overlap < 1 || o.overlap > 16) throw HzError{HZ_EINVAL, "overlap must be in [1, 16]"};
+    if (o.block_arnoldi != 0 && (o.block_arnoldi != 1 || o.max_block > 32))
+      throw HzError{HZ_EINVAL, "block_arnoldi needs max_block <= 32"};
     mesh_from_abi(fine, c->fine);
     mesh_build_adjacency(c->fine);
     const int64_t ne = c->fine.ne;
@@ -1152,6 +1233,7 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
     c->user_st = (cudaStream_t)stream;
     CK(cudaGetDevice(&c->device));
     CK(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
+    if (o.block_arnoldi) block_krylov_attrs();
     CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     join_user(c.get());
     c->space = p3_space(c->fine);
@@ -1169,16 +1251,19 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
       CoarseSpace C = build_coarse(c->fine, c->space, mvals, part, omega, c->coarse);
       c->cspace = C.space;
       // coarse level in FP64 unless the mixed form asks for an FP32 coarse level
+      // the coarse fronts are factorised in FP64 and, in the mixed form, applied in complex FP32 like
+      // the fine ones; E, Z and the inner coarse GMRES stay FP64 unless coarse_fp32 asks for FP32
       const bool cf32 = mixed && o.coarse_fp32 != 0;
+      c->coarse32 = cf32;
       upload_split(C.E, c->E, c->pool, c->st, cf32 && o.coarse_mode == HZ_COARSE_GMRES);
       upload_real(C.Z, c->Z, c->pool, c->st, cf32);
       upload_real(C.ZT, c->ZT, c->pool, c->st, cf32);
       if (o.coarse_mode == HZ_COARSE_GMRES) {
         std::vector<Subdomain> csubs =
             build_subdomains(c->coarse, c->cspace, C.part, nparts, C.mvals, omega, o.overlap);
-        build_level(c->cspace, csubs, o.leaf_size, cf32, tc, c->lc, c->pool, c->st);
+        build_level(c->cspace, csubs, o.leaf_size, mixed, tc, c->lc, c->pool, c->st);
       } else {
-        build_direct(c->cspace, C.E, o.leaf_size, cf32, tc, c->lc, c->pool, c->st);
+        build_direct(c->cspace, C.E, o.leaf_size, mixed, tc, c->lc, c->pool, c->st);
       }
     }
     CK(cudaStreamSynchronize(c->st));
@@ -1218,6 +1303,7 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
   if (rc != HZ_OK) {
     if (c) {
       if (c->st) cudaStreamSynchronize(c->st);
+      for (DevMF* mf : {&c->lf.mf, &c->lc.mf}) destroy_side(*mf);
       c->pool.release();
       if (c->st) cudaStreamDestroy(c->st);
       if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -1271,6 +1357,37 @@ int hz_column_stats(const hz_ctx* c, double* rel_residual, int32_t* iterations, 
     if (iterations) iterations[q] = c->col_its[q];
   }
   return HZ_OK;
+}
+
+int hz_krylov_basis(hz_ctx* c, double* V, int32_t cap, int32_t* nblocks, int32_t* ncols) {
+  if (!c || !nblocks || !ncols || cap < 0 || (cap > 0 && !V)) return fail(HZ_EINVAL, "bad argument");
+  if (c->s_cap == 0 || c->col_its.empty()) return fail(HZ_EINVAL, "no solve on this context yet");
+  return guarded([&]() -> int {
+    const int s = c->Kout.s;
+    const int64_t n = c->space.n;
+    int steps = 0;
+    if (c->opt.block_arnoldi) {
+      CK(cudaMemcpy(&steps, c->Bk.kb, sizeof(int), cudaMemcpyDeviceToHost));
+    } else {
+      std::vector<int> kc(s);
+      CK(cudaMemcpy(kc.data(), c->Kout.kc, s * sizeof(int), cudaMemcpyDeviceToHost));
+      for (int v : kc) steps = std::max(steps, v);
+    }
+    const int nb = std::min(steps + 1, c->opt.restart + 1);
+    *nblocks = nb;
+    *ncols = s;
+    std::vector<double2> blk((size_t)n * s);
+    for (int i = 0; i < std::min<int>(nb, cap); ++i) {
+      CK(cudaMemcpy(blk.data(), (double2*)c->Kout.V + (size_t)i * n * s, blk.size() * sizeof(double2),
+                    cudaMemcpyDeviceToHost));
+      for (int q = 0; q < s; ++q)
+        for (int64_t r = 0; r < n; ++r) {
+          V[2 * (((size_t)i * s + q) * n + r)] = blk[r * s + q].x;
+          V[2 * (((size_t)i * s + q) * n + r) + 1] = blk[r * s + q].y;
+        }
+    }
+    return HZ_OK;
+  });
 }
 
 int hz_profile_begin(hz_ctx* c) {
@@ -1487,6 +1604,7 @@ void hz_free(hz_ctx* c) {
   c->prof.destroy();
   c->g_fronts.reset();
   c->g_coarse.reset();
+  for (DevMF* mf : {&c->lf.mf, &c->lc.mf}) destroy_side(*mf);
   cudaStreamDestroy(c->st);
   cudaEventDestroy(c->ev_join);
   delete c;

@@ -78,8 +78,8 @@ struct DevMF {
   int* own = nullptr;           // [n] sub-vector row of the owning copy (D_i Boolean)
   int* perturbed = nullptr;     // device counter
   // tensor-core sweeps (complex FP32 form): tiles with at least TC_MIN_ROWS output rows and
-  // TC_MIN_K reduction indices run as tcgen05 MMAs (TF32 inputs, FP32 accumulation in TMEM)
-  // when the block has 16, 32 or 64 columns; the others keep the SIMT kernel
+  // TC_MIN_K reduction indices run as tcgen05 MMAs (three-term TF32 split, FP32 accumulation in
+  // TMEM) when the block has 9-16 columns; the others keep the SIMT kernel
   int tc = 0;                   // packed tensor-core tiles present
   int* fs_ptr_h = nullptr;      // host [nlevels+1] forward SIMT tiles per level (tensor-core mode)
   int* bs_ptr_h = nullptr;      // host [nlevels+1] backward SIMT tiles per level
@@ -95,6 +95,8 @@ struct DevMF {
   unsigned char* TC = nullptr;  // packed factor tiles (per 16-column chunk: Re plane, Im plane)
   int64_t tc_bytes = 0;
   int* tc_err = nullptr;        // device flag: a tensor-core tile gave up waiting on a barrier
+  cudaStream_t side = nullptr;  // tensor-core mode: the SIMT tiles of a level run here, beside the tcgen05 tiles
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 // tensor-core tile eligibility (output rows, reduction length) and packing geometry
@@ -151,6 +153,35 @@ struct DevKrylov {
   int* reorth = nullptr;    // [s] second Gram-Schmidt pass needed
   int nblk = 0;
 };
+
+// --- block Krylov (one Krylov space shared by the s columns; FP64, s <= 32) ---
+struct DevBlockKrylov {
+  int m = 0, s = 0, nblk = 0;
+  int64_t n = 0;
+  double2* V = nullptr;      // [(m+1)][n][s] orthonormal basis blocks (the per-column form's arrays)
+  double2* Zk = nullptr;     // [m][n][s] preconditioned blocks
+  double2* W = nullptr;      // [n][s]
+  double2* Hd = nullptr;     // block Hessenberg, column-major ((m+1) s) x (m s), rotated in place
+  double2* Gr = nullptr;     // rotated right-hand side, column-major ((m+1) s) x s
+  double* rc = nullptr;      // Givens cosines [m s][s]
+  double2* rsn = nullptr;    // Givens sines [m s][s]
+  double2* part = nullptr;   // partial Gram blocks [nblk][m+1][s][s]
+  double2* h1 = nullptr;     // [m+1][s][s] first Gram-Schmidt pass
+  double2* h2 = nullptr;     // [m+1][s][s] second pass
+  double2* gram = nullptr;   // [s][s]
+  double2* R = nullptr;      // [s][s] one CholQR factor
+  double2* Racc = nullptr;   // [s][s] R2 R1
+  double2* Y = nullptr;      // [s][m s] least-squares coefficients
+  double* res = nullptr;     // [s] residual estimates
+  double* tol = nullptr;     // [s]
+  int* done = nullptr;       // [s]
+  int* kb = nullptr;         // accepted block steps
+  int* deflated = nullptr;   // directions dropped by CholQR in the current cycle
+};
+void block_krylov_start(DevBlockKrylov& B, double2* R, cudaStream_t st);  // V0 S0 = R (R overwritten), G = [S0; 0]
+void block_krylov_arnoldi(DevBlockKrylov& B, int j, cudaStream_t st);     // CGS2 + CholQR2, Hessenberg, Givens
+void block_krylov_update(DevBlockKrylov& B, double2* X, cudaStream_t st); // X += Z Y
+void block_krylov_attrs();
 
 void column_norms(const void* X, int64_t n, int s, double* out, DevKrylov& K, cudaStream_t st);
 void krylov_start(DevKrylov& K, const void* R, cudaStream_t st);  // V0 = R/beta, g = beta e1, flags

@@ -233,7 +233,7 @@ void mf_factor(DevMF& mf, double tau_abs, cudaStream_t st) {
   if (mf.tc && mf.fp32) tc_pack_all(mf, st);
 }
 
-bool mf_tc_usable(const DevMF& mf, int s) { return mf.tc && mf.fp32 && s > 8 && s <= 64; }
+bool mf_tc_usable(const DevMF& mf, int s) { return mf.tc && mf.fp32 && s > 8 && s <= 16; }
 
 // ---------------------------------------------------------------------------
 // Solve sweeps
@@ -443,22 +443,30 @@ __global__ void k_mf_reduce(const int4* __restrict__ rblocks, int nrb, const int
 }
 
 // ---------------------------------------------------------------------------
-// Tensor-core tiles (complex FP32 form): the same tile product on tcgen05.
+// Tensor-core tiles (complex FP32 form): the same tile product on tcgen05,
+// with FP32 accuracy from a three-term TF32 split (Markidis et al. 2018:
+// a = a_hi + a_lo with a_hi = a rounded to TF32, a_lo = a - a_hi also in
+// TF32; a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi, the dropped a_lo b_lo being
+// ~2^-22 relative).
 //
 // The tile's factor block is packed once, after the factorisation, as
 // 16-column chunks; each chunk holds a real and an imaginary plane of
-// nr8 = roundup(rows, 8) rows x 16 reduction indices, TF32-rounded, in the
+// nr8 = roundup(rows, 8) rows x 16 reduction indices in FP32, in the
 // K-major layout of 8-row x 16-byte core matrices (a row group's 4 core
 // matrices are adjacent, row groups 512 bytes apart), reduction indices past
 // the tile's end zero. A chunk is two contiguous copies (cp.async.bulk) into
-// a two-stage shared-memory ring. The input rows are staged as two N x 128
-// operands, N = 2S: B1 = [Re b | Im b] and B2 = [-Im b | Re b], so that
+// a ring of shared-memory stages; once it has landed, the CTA truncates it
+// in place to its TF32 high part and writes the low part beside it. The input
+// rows are staged once per tile as N x 128 operands, N = 2S, in high and low
+// parts: B1 = [Re b | Im b] and B2 = [-Im b | Re b], so that
 //   D = Re(M) B1^T + Im(M) B2^T = [Re(M b) | Im(M b)]
-// accumulates in TMEM (128 lanes = output rows, N columns, FP32). One thread
-// issues the MMAs (M = 128, N = 2S, K = 8 per instruction) and commits them
-// to the ring's barriers; every wait is bounded and a timeout sets tc_err.
-// Rows past the tile's end hold stale shared memory; their outputs are never
-// written.
+// accumulates in TMEM (128 lanes = output rows, N columns, FP32). Thread 0
+// issues the MMAs (M = 128, N = 2S, K = 8 per instruction, 6 per 8 reduction
+// indices) and commits them to the ring's barriers. Every wait is bounded by
+// the global timer; a timeout sets *err, skips the epilogue, and the CTA
+// waits (bounded again) for its copies in flight and its MMAs before it
+// frees its TMEM and exits. Rows past the tile's end hold stale shared
+// memory; their outputs are never written.
 // ---------------------------------------------------------------------------
 constexpr int TC_PLANE = 8192;              // one plane of a 128-row chunk in shared memory
 constexpr int TC_STAGE = 2 * TC_PLANE;      // a chunk (real + imaginary plane)
@@ -471,22 +479,29 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_
   return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
+__device__ __forceinline__ uint64_t tc_clock_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// wait for phase `parity` of an mbarrier, giving up after about half a second
 __device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
   uint32_t done = 0;
-  for (long it = 0; it < (1L << 24) && !done; ++it)
+  const uint64_t t0 = tc_clock_ns();
+  while (!done) {
     asm volatile(
         "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}\n"
         : "=r"(done)
         : "r"(bar), "r"(parity)
         : "memory");
-  return done != 0;
+    if (!done && tc_clock_ns() - t0 > 500000000ull) return false;
+  }
+  return true;
 }
-__device__ __forceinline__ float tc_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
+// TF32 value of x by truncation of the 13 low mantissa bits: the high part
+// of the split, exactly representable in TF32, with x - hi exact in FP32
+__device__ __forceinline__ float tc_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 // byte offset of element (row, col) in a K-major core-matrix tile whose row
 // groups are sbo bytes apart
 __device__ __forceinline__ int tc_off(int row, int col, int sbo) {
@@ -517,7 +532,7 @@ __device__ __forceinline__ TcGeom tc_geom(int4 tile, const int* kk, const int* f
   return g;
 }
 
-// Pack the factor blocks of the tensor-core tiles (after k_mf_inverse).
+// Pack the factor blocks of the tensor-core tiles (after k_mf_inverse), FP32.
 template <bool FWD>
 __global__ void k_tc_pack(const int4* __restrict__ tiles, const int64_t* __restrict__ off, const int* __restrict__ kk,
                           const int* __restrict__ ff, const int64_t* __restrict__ Moff, const float2* __restrict__ M,
@@ -536,8 +551,8 @@ __global__ void k_tc_pack(const int4* __restrict__ tiles, const int64_t* __restr
     if (m < g.nr && col < g.kstop) v = Mt[(g.r0 + m) + (int64_t)col * g.ld];
     unsigned char* ch = base + (int64_t)q * 2 * plane;
     const int o = tc_off(m, kc, TC_SBO_A);
-    *reinterpret_cast<float*>(ch + o) = tc_tf32(v.x);
-    *reinterpret_cast<float*>(ch + plane + o) = tc_tf32(v.y);
+    *reinterpret_cast<float*>(ch + o) = v.x;
+    *reinterpret_cast<float*>(ch + plane + o) = v.y;
   }
 }
 
@@ -550,11 +565,32 @@ static void tc_pack_all(DevMF& mf, cudaStream_t st) {
                                                           (const float2*)mf.MT, mf.TC); count_launch(); }
 }
 
+// shared memory of the tensor-core tile (96 KB, two CTAs per SM): the input
+// operand B = [Re b | Im b] (N x 128) in high and low parts, a ring of
+// TC_NRAW raw factor chunks and one working chunk (high part | low part)
+// that the MMAs read
+constexpr int TC_NRAW = 2;
 template <int S>
 static constexpr size_t tc_smem_bytes() {
-  return 2 * (size_t)(2 * S) * MF_TK * 4 + 2 * (size_t)TC_STAGE;
+  return 2 * (size_t)(2 * S) * MF_TK * 4 + (size_t)TC_NRAW * TC_STAGE + 2 * (size_t)TC_STAGE;
 }
 
+__device__ __forceinline__ void tc_mma(uint32_t taddr, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(taddr),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+// Complex product on real MMAs: D1 = Re(M) B and D2 = Im(M) B accumulate in
+// two TMEM blocks of N = 2S columns; the epilogue forms
+//   Re(M b) = D1[:, 0:S] - D2[:, S:2S],  Im(M b) = D1[:, S:2S] + D2[:, 0:S].
+// Chunk pipeline (128 threads): thread 0 keeps TC_NRAW raw chunks in flight;
+// every thread waits for chunk q and for the MMAs of chunk q - 1 (which read
+// the working buffer), splits the raw chunk into its high and low parts in
+// the working buffer, and after a CTA barrier (which also frees the raw stage
+// for the copy of chunk q + TC_NRAW) thread 0 issues the six MMAs per 8
+// reduction indices and commits them to the working buffer's barrier.
 template <int S, bool FWD>
 __global__ void __launch_bounds__(MF_TILE) k_mf_tile_tc(
     const int4* __restrict__ tiles, const int64_t* __restrict__ tcoff, const unsigned char* __restrict__ TC,
@@ -562,31 +598,35 @@ __global__ void __launch_bounds__(MF_TILE) k_mf_tile_tc(
     const int* __restrict__ rows, const int64_t* __restrict__ cptr, const int* __restrict__ cidx,
     const int64_t* __restrict__ Doff, const float2* __restrict__ Dinv, float2* __restrict__ Xsub,
     float2* __restrict__ Wout, float2* __restrict__ P, int s, int* __restrict__ err) {
+  static_assert(S == 16, "tensor-core tiles are built for blocks of 16 columns");
   constexpr int N = 2 * S;
   constexpr int BT = N * MF_TK * 4;
-  constexpr uint32_t NCOL = N < 32 ? 32 : N;
+  constexpr uint32_t NCOL = 2 * N;  // D1 and D2
   extern __shared__ __align__(1024) unsigned char smem_tc[];
-  unsigned char* sB1 = smem_tc;
-  unsigned char* sB2 = smem_tc + BT;
-  unsigned char* stg = smem_tc + 2 * BT;
-  __shared__ __align__(8) uint64_t full[2], freeb[2], done;
+  unsigned char* sBh = smem_tc;
+  unsigned char* sBl = smem_tc + BT;
+  unsigned char* raw = smem_tc + 2 * BT;            // TC_NRAW x TC_STAGE
+  unsigned char* wh = raw + TC_NRAW * TC_STAGE;     // working chunk, high part (real plane, imaginary plane)
+  unsigned char* wl = wh + TC_STAGE;                // low part
+  __shared__ __align__(8) uint64_t full[TC_NRAW], freeb, done;
   __shared__ uint32_t tslot;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const TcGeom g = tc_geom<FWD>(tiles[blockIdx.x], kk, ff);
   const unsigned char* src = TC + tcoff[blockIdx.x];
   const uint32_t plane = (uint32_t)g.nr8 * 64, cbytes = 2 * plane;
   if (tid == 0) {
-    for (int i = 0; i < 2; ++i) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&full[i])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&freeb[i])));
-    }
+    for (int i = 0; i < TC_NRAW; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&full[i])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&freeb)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&done)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_ok = 1;
   }
   __syncthreads();
-  auto load_chunk = [&](int q) {  // thread 0: chunk q into stage q & 1
-    const uint32_t bar = tc_smem(&full[q & 1]);
-    const uint32_t dst = tc_smem(stg + (q & 1) * TC_STAGE);
+  int issued = 0;  // thread 0: chunks whose copies were issued
+  auto load_chunk = [&](int q) {  // thread 0: chunk q into raw stage q % TC_NRAW
+    const uint32_t bar = tc_smem(&full[q % TC_NRAW]);
+    const uint32_t dst = tc_smem(raw + (q % TC_NRAW) * TC_STAGE);
     const unsigned char* c = src + (int64_t)q * cbytes;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(cbytes) : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -596,15 +636,16 @@ __global__ void __launch_bounds__(MF_TILE) k_mf_tile_tc(
                      dst + TC_PLANE),
                  "l"(c + plane), "r"(plane), "r"(bar)
                  : "memory");
+    issued = q + 1;
   };
   if (tid == 0)
-    for (int q = 0; q < min(2, g.nch); ++q) load_chunk(q);
+    for (int q = 0; q < min(TC_NRAW, g.nch); ++q) load_chunk(q);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(&tslot)),
                  "r"(NCOL));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  // input rows -> B1 = [Re | Im], B2 = [-Im | Re] (TF32), zero past the tile's reduction end
+  // input rows -> high and low parts of B = [Re | Im], zero past the tile's reduction end
   const int64_t ro = rowoff[g.t];
   if (tid < g.nch * 16) {
     const int l = tid;
@@ -630,91 +671,104 @@ __global__ void __launch_bounds__(MF_TILE) k_mf_tile_tc(
     }
 #pragma unroll
     for (int c = 0; c < S; ++c) {
-      const float re = tc_tf32(v[c].x), im = tc_tf32(v[c].y);
-      *reinterpret_cast<float*>(sB1 + tc_off(c, l, TC_SBO_B)) = re;
-      *reinterpret_cast<float*>(sB1 + tc_off(S + c, l, TC_SBO_B)) = im;
-      *reinterpret_cast<float*>(sB2 + tc_off(c, l, TC_SBO_B)) = -im;
-      *reinterpret_cast<float*>(sB2 + tc_off(S + c, l, TC_SBO_B)) = re;
+      const float reh = tc_hi(v[c].x), imh = tc_hi(v[c].y);
+      const int o0 = tc_off(c, l, TC_SBO_B), o1 = tc_off(S + c, l, TC_SBO_B);
+      *reinterpret_cast<float*>(sBh + o0) = reh;
+      *reinterpret_cast<float*>(sBh + o1) = imh;
+      *reinterpret_cast<float*>(sBl + o0) = tc_hi(v[c].x - reh);
+      *reinterpret_cast<float*>(sBl + o1) = tc_hi(v[c].y - imh);
     }
   }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B: generic writes, async-proxy reads
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t taddr = tslot;
   // kind::tf32: D f32, A and B tf32, both K-major, N = 2S, M = 128
   constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-  bool ok = true;
-  if (tid == 0) {
-    for (int q = 0; q < g.nch && ok; ++q) {
-      const int sidx = q & 1;
-      const uint32_t ph = (q >> 1) & 1;
-      ok = tc_wait(tc_smem(&full[sidx]), ph);
-      if (!ok) break;
+  const int per_plane = g.nr8 * 16;  // floats of one plane of a chunk
+  for (int q = 0; q < g.nch; ++q) {
+    const int r = q % TC_NRAW;
+    bool okq = tc_wait(tc_smem(&full[r]), (q / TC_NRAW) & 1);
+    if (okq && q >= 1) okq = tc_wait(tc_smem(&freeb), (q - 1) & 1);  // MMAs of chunk q - 1 done
+    if (!okq) s_ok = 0;
+    if (okq)
+      for (int i = tid; i < 2 * per_plane; i += MF_TILE) {
+        const int pl = i >= per_plane, e = i - pl * per_plane;
+        const float x = *(reinterpret_cast<const float*>(raw + r * TC_STAGE + pl * TC_PLANE) + e);
+        const float h = tc_hi(x);
+        *(reinterpret_cast<float*>(wh + pl * TC_PLANE) + e) = h;
+        *(reinterpret_cast<float*>(wl + pl * TC_PLANE) + e) = tc_hi(x - h);
+      }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (!s_ok) break;
+    if (tid == 0) {
+      // every thread has read raw stage r: it takes the copy of chunk q + TC_NRAW
+      if (q + TC_NRAW < g.nch) load_chunk(q + TC_NRAW);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t aRe = tc_smem(stg + sidx * TC_STAGE), aIm = aRe + TC_PLANE;
+      const uint32_t aReH = tc_smem(wh), aImH = aReH + TC_PLANE, aReL = tc_smem(wl), aImL = aReL + TC_PLANE;
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        const uint64_t dRe = tc_desc(aRe + j * 256, 128, TC_SBO_A);
-        const uint64_t dIm = tc_desc(aIm + j * 256, 128, TC_SBO_A);
         const uint32_t kb = (uint32_t)(q * 4 + 2 * j) * 128;
-        const uint64_t d1 = tc_desc(tc_smem(sB1) + kb, 128, TC_SBO_B);
-        const uint64_t d2 = tc_desc(tc_smem(sB2) + kb, 128, TC_SBO_B);
-        const uint32_t acc = (q > 0 || j > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(taddr),
-            "l"(dRe), "l"(d1), "r"(idesc), "r"(acc));
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(taddr),
-            "l"(dIm), "l"(d2), "r"(idesc), "r"(1u));
+        const uint64_t dReH = tc_desc(aReH + j * 256, 128, TC_SBO_A), dImH = tc_desc(aImH + j * 256, 128, TC_SBO_A);
+        const uint64_t dReL = tc_desc(aReL + j * 256, 128, TC_SBO_A), dImL = tc_desc(aImL + j * 256, 128, TC_SBO_A);
+        const uint64_t dbh = tc_desc(tc_smem(sBh) + kb, 128, TC_SBO_B), dbl = tc_desc(tc_smem(sBl) + kb, 128, TC_SBO_B);
+        const uint32_t first = (q > 0 || j > 0) ? 1u : 0u;
+        tc_mma(taddr, dReH, dbh, idesc, first);
+        tc_mma(taddr, dReH, dbl, idesc, 1u);
+        tc_mma(taddr, dReL, dbh, idesc, 1u);
+        tc_mma(taddr + N, dImH, dbh, idesc, first);
+        tc_mma(taddr + N, dImH, dbl, idesc, 1u);
+        tc_mma(taddr + N, dImL, dbh, idesc, 1u);
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       tc_smem(&freeb[sidx]))
+                       tc_smem(&freeb))
                    : "memory");
-      if (q + 2 < g.nch) {
-        ok = tc_wait(tc_smem(&freeb[sidx]), ph);  // the MMAs reading this stage have completed
-        if (!ok) break;
-        load_chunk(q + 2);
-      }
     }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     tc_smem(&done))
-                 : "memory");
   }
-  __syncwarp();
+  // `done` arrives once every MMA issued so far has completed
+  if (tid == 0)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc_smem(&done))
+                 : "memory");
   const bool fin = tc_wait(tc_smem(&done), 0);
-  if (!fin || !ok) atomicExch(err, 1);
+  if (!fin) s_ok = 0;
+  __syncthreads();
+  const bool ok = s_ok != 0;
+  if (!ok && tid == 0) {
+    atomicExch(err, 1);
+    // copies still in flight must land before the CTA's shared memory is released (bounded waits;
+    // a stage whose chunk was already consumed passes at once)
+    for (int q = max(0, issued - TC_NRAW); q < issued; ++q) tc_wait(tc_smem(&full[q % TC_NRAW]), (q / TC_NRAW) & 1);
+  }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (fin) {
+  if (ok) {
     const int m = tid;  // TMEM lane = output row of the tile
     const bool act = m < g.nr;
     const int rr = g.r0 + m;
     const int64_t Rg = ro + rr;
     const uint32_t lane_base = taddr + ((uint32_t)(warp * 32) << 16);
+    uint32_t d1r[16], d1i[16], d2r[16], d2i[16];
+#define HZ_TMEM_LD16(dst, col)                                                                                      \
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];" \
+               : "=r"(dst[0]), "=r"(dst[1]), "=r"(dst[2]), "=r"(dst[3]), "=r"(dst[4]), "=r"(dst[5]), "=r"(dst[6]),     \
+                 "=r"(dst[7]), "=r"(dst[8]), "=r"(dst[9]), "=r"(dst[10]), "=r"(dst[11]), "=r"(dst[12]), "=r"(dst[13]), \
+                 "=r"(dst[14]), "=r"(dst[15])                                                                       \
+               : "r"(lane_base + (col)))
+    HZ_TMEM_LD16(d1r, 0);
+    HZ_TMEM_LD16(d1i, S);
+    HZ_TMEM_LD16(d2r, N);
+    HZ_TMEM_LD16(d2i, N + S);
+#undef HZ_TMEM_LD16
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (act) {
 #pragma unroll
-    for (int g16 = 0; g16 < S / 16; ++g16) {
-      uint32_t re[16], im[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]), "=r"(re[6]), "=r"(re[7]),
-            "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]), "=r"(re[12]), "=r"(re[13]), "=r"(re[14]),
-            "=r"(re[15])
-          : "r"(lane_base + g16 * 16));
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]), "=r"(im[6]), "=r"(im[7]),
-            "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]), "=r"(im[12]), "=r"(im[13]), "=r"(im[14]),
-            "=r"(im[15])
-          : "r"(lane_base + S + g16 * 16));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (!act) continue;
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int c = g16 * 16 + u;
+      for (int c = 0; c < S; ++c) {
         if (c >= s) break;
-        float2 a = make_float2(__uint_as_float(re[u]), __uint_as_float(im[u]));
+        // Re(M b) = Re M Re b - Im M Im b,  Im(M b) = Re M Im b + Im M Re b
+        float2 a = make_float2(__uint_as_float(d1r[c]) - __uint_as_float(d2i[c]),
+                               __uint_as_float(d1i[c]) + __uint_as_float(d2r[c]));
         if (g.slot >= 0) {
           P[((int64_t)g.slot * MF_TILE + m) * s + c] = a;
         } else if (FWD) {
@@ -740,7 +794,7 @@ static inline unsigned blocks_for(int64_t work, int b) { return (unsigned)((work
 
 template <typename V, int S>
 static constexpr bool tc_width() {
-  return std::is_same<V, float2>::value && S >= 16;
+  return std::is_same<V, float2>::value && S == 16;
 }
 
 template <typename V, int S, bool FWD>
@@ -774,12 +828,28 @@ static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
   const int* bptr = tc ? mf.bs_ptr_h : mf.btile_ptr_h;
   const int4* ftl = tc ? mf.ftiles_s : mf.ftiles;
   const int4* btl = tc ? mf.btiles_s : mf.btiles;
+  // tensor-core mode: a level's SIMT tiles run on the side stream, concurrently with its tcgen05 tiles
+  // (they write disjoint outputs and partial slots); the level's reduce waits for both
+  const bool fork = tc && mf.side;
+  auto fork_begin = [&]() {
+    if (!fork) return st;
+    cudaEventRecord(mf.ev_fork, st);
+    cudaStreamWaitEvent(mf.side, mf.ev_fork, 0);
+    return mf.side;
+  };
+  auto fork_end = [&]() {
+    if (!fork) return;
+    cudaEventRecord(mf.ev_join, mf.side);
+    cudaStreamWaitEvent(st, mf.ev_join, 0);
+  };
   for (int l = 0; l < mf.nlevels; ++l) {
     const int tb = fptr[l], te = fptr[l + 1];
+    cudaStream_t ss = fork_begin();
     if (te > tb)
-      { k_mf_tile<V, S, true><<<te - tb, MF_TILE, shm, st>>>(ftl + tb, mf.k, mf.f, mf.rowoff, mf.Moff, M, mf.rows,
+      { k_mf_tile<V, S, true><<<te - tb, MF_TILE, shm, ss>>>(ftl + tb, mf.k, mf.f, mf.rowoff, mf.Moff, M, mf.rows,
                                                              mf.cptr, mf.cidx, mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
     if (tc) tc_launch<V, S, true>(mf, l, Xsub, s, st);
+    fork_end();
     const int rb = mf.frb_ptr_h[l], re = mf.frb_ptr_h[l + 1];
     if (re > rb)
       { k_mf_reduce<V, true><<<blocks_for((int64_t)(re - rb) * MF_TILE * s, 256), 256, 0, st>>>(
@@ -787,10 +857,12 @@ static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
   }
   for (int l = mf.nlevels - 1; l >= 0; --l) {
     const int tb = bptr[l], te = bptr[l + 1];
+    cudaStream_t ss = fork_begin();
     if (te > tb)
-      { k_mf_tile<V, S, false><<<te - tb, MF_TILE, shm, st>>>(btl + tb, mf.k, mf.f, mf.rowoff, mf.Moff, MT,
+      { k_mf_tile<V, S, false><<<te - tb, MF_TILE, shm, ss>>>(btl + tb, mf.k, mf.f, mf.rowoff, mf.Moff, MT,
                                                               mf.rows, mf.cptr, mf.cidx, mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
     if (tc) tc_launch<V, S, false>(mf, l, Xsub, s, st);
+    fork_end();
     const int rb = mf.brb_ptr_h[l], re = mf.brb_ptr_h[l + 1];
     if (re > rb)
       { k_mf_reduce<V, false><<<blocks_for((int64_t)(re - rb) * MF_TILE * s, 256), 256, 0, st>>>(

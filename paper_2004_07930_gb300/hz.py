@@ -21,7 +21,7 @@ EXPORTS = ["hz_default_options", "hz_setup", "hz_ndof", "hz_dof_coords", "hz_get
            "hz_solve_rhs", "hz_apply_A", "hz_apply_prec", "hz_matrix_csr", "hz_free", "hz_strerror",
            "hz_last_error", "hz_profile_begin", "hz_profile_end", "hz_apply_A_noalloc", "hz_server_create",
            "hz_server_submit", "hz_server_step", "hz_server_fetch", "hz_server_pending", "hz_server_free",
-           "hz_receiver_operator", "hz_fwi_gradient", "hz_column_stats"]
+           "hz_receiver_operator", "hz_fwi_gradient", "hz_column_stats", "hz_krylov_basis"]
 HZ_NOALLOC_MAX_ENTRIES = 1048576  # complex entries per work block of hz_apply_A_noalloc (n * s)
 
 
@@ -35,7 +35,7 @@ class HzOptions(C.Structure):
                 ("max_block", C.c_int32), ("coarse_mode", C.c_int32), ("coarse_inner_its", C.c_int32),
                 ("leaf_size", C.c_int32), ("pivot_tau", C.c_double), ("verbose", C.c_int32),
                 ("use_graphs", C.c_int32), ("tensor_cores", C.c_int32), ("overlap", C.c_int32),
-                ("coarse_fp32", C.c_int32), ("debug_bounds", C.c_int32)]
+                ("coarse_fp32", C.c_int32), ("debug_bounds", C.c_int32), ("block_arnoldi", C.c_int32)]
 
 
 class HzStats(C.Structure):
@@ -103,6 +103,7 @@ def load():
     lib.hz_receiver_operator.argtypes = [P, P, C.c_int32, P, P]
     lib.hz_fwi_gradient.argtypes = [P, P, P, C.c_int32, P, C.c_int32, P, P, P, P, C.POINTER(HzStats)]
     lib.hz_column_stats.argtypes = [P, P, P, C.c_int32, C.POINTER(C.c_int32)]
+    lib.hz_krylov_basis.argtypes = [P, P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.hz_profile_begin.argtypes = [P]
     lib.hz_profile_end.argtypes = [P, C.POINTER(HzPhaseTime), C.c_int32, C.POINTER(C.c_int32)]
     lib.hz_free.argtypes = [P]
@@ -235,6 +236,14 @@ class Solver:
         its = np.empty(nc.value, dtype=np.int32)
         _check(self._lib.hz_column_stats(self._ctx, res.ctypes.data, its.ctypes.data, nc.value, C.byref(nc)))
         return res, its
+
+    def krylov_basis(self):
+        """Basis of the last restart cycle: array [nblocks, ncols, n] complex."""
+        nb, nc = C.c_int32(), C.c_int32()
+        _check(self._lib.hz_krylov_basis(self._ctx, None, 0, C.byref(nb), C.byref(nc)))
+        V = np.empty((nb.value, nc.value, self.n), dtype=np.complex128)
+        _check(self._lib.hz_krylov_basis(self._ctx, V.ctypes.data, nb.value, C.byref(nb), C.byref(nc)))
+        return V
 
     def profile_begin(self):
         _check(self._lib.hz_profile_begin(self._ctx))

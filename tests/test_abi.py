@@ -67,6 +67,7 @@ def test_setup_rejects_bad_inputs(lib):
     assert _setup_rc(p, freq=0.0) == hz.HZ_EINVAL
     assert _setup_rc(p, overlap=0) == hz.HZ_EINVAL
     assert _setup_rc(p, overlap=17) == hz.HZ_EINVAL
+    assert _setup_rc(p, block_arnoldi=1, max_block=64) == hz.HZ_EINVAL     # block FGMRES: max_block <= 32
     assert "partition" in hz.load().hz_last_error().decode() or True
     assert lib.hz_strerror(hz.HZ_ENOTCONV).decode() == "not converged"
 

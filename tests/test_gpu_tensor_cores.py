@@ -1,8 +1,10 @@
 """Tensor-core front sweeps (mixed form, tensor_cores = 1): the local solves
-use TF32-rounded factors with FP32 accumulation, so the preconditioner is a
-perturbation of the FP32 one of relative size ~1e-3; FGMRES in FP64 still
-converges to the oracle's discrete solution. Blocks of 16 and 32 columns run
-the tensor-core kernels; blocks of at most 8 columns keep the SIMT sweeps."""
+run as tcgen05 MMAs on a three-term TF32 split of the FP32 factors and
+inputs (hi*hi + hi*lo + lo*hi, FP32 accumulation), so the preconditioner
+keeps FP32 accuracy: within 1e-5 of the exact Eq. oras operator (the plain
+SIMT FP32 sweeps: ~3e-7; a single TF32 product: ~3e-4), and FGMRES needs the
+same iterations as with the SIMT sweeps. Blocks of 9-16 columns run the
+tensor-core kernels; narrower and wider blocks keep the SIMT sweeps."""
 import numpy as np
 import pytest
 
@@ -27,7 +29,7 @@ def _sources(ns, seed):
     return rng.uniform(80.0, 920.0, size=(ns, 3))
 
 
-@pytest.mark.parametrize("s", [16, 32])
+@pytest.mark.parametrize("s", [16, 12])
 def test_preconditioner_close_to_oracle(cube, s):
     T = osw.TwoLevel(cube, coarse_mode="none")
     opts = dict(precision=hz.HZ_PREC_MIXED, coarse_mode=hz.HZ_COARSE_NONE)
@@ -44,8 +46,8 @@ def test_preconditioner_close_to_oracle(cube, s):
     e_tc, e_s = rel_l2(Yt, ref).max(), rel_l2(Ys, ref).max()
     print("s", s, "tensor-core vs SIMT FP32: %.3e; vs exact: tensor cores %.3e, SIMT %.3e" % (d.max(), e_tc, e_s))
     assert d.max() > 1e-8                                   # the tensor-core tiles did run
-    assert e_s <= 1e-4
-    assert e_tc <= 5e-2
+    assert e_s <= 1e-5
+    assert e_tc <= 1e-5
 
 
 @pytest.mark.parametrize("coarse", [hz.HZ_COARSE_NONE, hz.HZ_COARSE_GMRES])
@@ -63,14 +65,15 @@ def test_wavefields_match_oracle(cube, coarse):
             assert st["converged"] == 1
             assert rel_l2(u, u_or[:, perm]).max() <= 1e-6
     print("coarse", coarse, "iterations SIMT", its[0], "tensor cores", its[1])
-    assert its[1] <= 1.5 * its[0] + 3
+    assert its[1] <= its[0] + 1
 
 
-def test_narrow_blocks_keep_simt(cube):
-    """s <= 8 runs the SIMT sweeps even with tensor_cores = 1: identical
-    preconditioner to tensor_cores = 0."""
+@pytest.mark.parametrize("s", [4, 24])
+def test_other_widths_keep_simt(cube, s):
+    """Blocks of at most 8 or more than 16 columns run the SIMT sweeps even
+    with tensor_cores = 1: identical preconditioner to tensor_cores = 0."""
     opts = dict(precision=hz.HZ_PREC_MIXED, coarse_mode=hz.HZ_COARSE_NONE)
     with hz.Solver.from_problem(cube, tensor_cores=1, **opts) as St, \
             hz.Solver.from_problem(cube, tensor_cores=0, **opts) as Ss:
-        X = wl.random_rhs(St.n, 4, 8)
+        X = wl.random_rhs(St.n, s, 8)
         np.testing.assert_array_equal(St.apply_prec(X), Ss.apply_prec(X))
