@@ -133,7 +133,10 @@ def parse():
     ap.add_argument("--serving-freqs", default="3.5,5,7")
     ap.add_argument("--serving-requests", type=int, default=400)
     ap.add_argument("--serving-rate", type=float, default=2.0, help="mean request arrivals per second")
-    ap.add_argument("--serving-slots", type=int, default=32, help="right-hand-side slots per frequency")
+    ap.add_argument("--serving-slots", type=int, default=32, help="right-hand-side slots per frequency "
+                    "(when --serving-budget-gb is 0)")
+    ap.add_argument("--serving-budget-gb", type=float, default=60.0,
+                    help="device bytes shared by the servers' slots (admission by footprint); 0: fixed slots")
     ap.add_argument("--serving-coarse", choices=["gmres", "none", "direct"], default="none",
                     help="coarse level of the serving solvers (one-level ORAS by default: on these meshes it "
                          "converges in fewer iterations than the two-level form)")
@@ -306,11 +309,12 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def serving_stream(S, hz, rhs_per_s, nreq=24, load=0.8, seed=11):
+def serving_stream(S, hz, rhs_per_s, nreq=24, load=0.8, seed=11, budget_gb=40.0):
     """A short seeded Poisson stream through the continuous-batching server
     on the solver S: nreq requests of 1-16 point sources at uniform surface
     positions (z = 100 m), offered at `load` x the measured saturated rate
-    rhs_per_s. Returns RHS/s and p50/p99 latency (arrival to completion)."""
+    rhs_per_s, slots admitted by device footprint within budget_gb. Returns
+    RHS/s and p50/p99 latency (arrival to completion)."""
     import numpy as np
 
     from paper_2004_07930_gb300.serve import ServingLoop
@@ -323,10 +327,11 @@ def serving_stream(S, hz, rhs_per_s, nreq=24, load=0.8, seed=11):
     for i in range(nreq):
         xy = rng.uniform(1000.0, 19000.0, size=(nsrc[i], 2))
         reqs.append((float(arrival[i]), i, 0, np.concatenate([xy, np.full((nsrc[i], 1), 100.0)], axis=1)))
-    loop = ServingLoop({0: S}, 32)
+    loop = ServingLoop({0: S}, device_budget=budget_gb * 1e9)
     summ = loop.run_stream(reqs)
     loop.close()
-    summ.update({"offered_load": load, "offered_rhs_per_s": load * rhs_per_s, "slots": 32,
+    summ.update({"offered_load": load, "offered_rhs_per_s": load * rhs_per_s, "slot_budget_gb": budget_gb,
+                 "column_gb": S.column_bytes() / 1e9,
                  "stream": "%d requests, 1-16 sources each, Poisson arrivals (PCG64 seed %d)" % (nreq, seed)})
     return summ
 
@@ -465,7 +470,10 @@ def run_serving(args):
         xy = rng.uniform(1000.0, 19000.0, size=(nsrc[i], 2))
         src = np.concatenate([xy, np.full((nsrc[i], 1), 100.0)], axis=1)
         reqs.append((float(arrival[i]), i, freqs[fsel[i]], src))
-    loop = ServingLoop(solvers, args.serving_slots)
+    if args.serving_budget_gb > 0:
+        loop = ServingLoop(solvers, device_budget=args.serving_budget_gb * 1e9)
+    else:
+        loop = ServingLoop(solvers, args.serving_slots)
     dev_gb = sum(S.info()["device_bytes"] for S in solvers.values()) / 1e9
     launches0 = next(iter(solvers.values())).info()["kernel_launches"]  # process-wide counter
     clocks = ClockSampler(0)
@@ -482,7 +490,8 @@ def run_serving(args):
             "data": "synthetic (seeded Overthrust-like model and request stream)",
             "config": {"workload": "Overthrust-like, f in %s Hz, n %s, 64 subdomains, Poisson arrivals %.2f/s, "
                                    "1-32 sources per request" % (freqs, [sizes[f] for f in freqs], args.serving_rate),
-                       "slots_per_frequency": args.serving_slots, "device_gb": dev_gb,
+                       "slots_per_frequency": summ.get("slots"), "device_gb": dev_gb,
+                       "slot_budget_gb": args.serving_budget_gb,
                        "coarse": args.serving_coarse, "setup_s": {str(f): setup[f] for f in freqs}},
             "clocks": clk, "gpu_launches": launches}
     print(json.dumps(line), flush=True)

@@ -253,6 +253,11 @@ int hz_profile_end(hz_ctx* ctx, hz_phase_time* out, int32_t cap, int32_t* count)
  * mesh), HZ_ENOMEM, HZ_ECUDA. */
 typedef struct hz_server hz_server;
 int hz_server_create(hz_ctx* ctx, int32_t slots, hz_server** out);
+/* Device bytes one slot (right-hand-side column) of a server on ctx costs:
+ * the server's blocks plus the context workspace of one column (Krylov basis,
+ * preconditioner blocks, local sub-vectors of both levels). A caller admits by
+ * device footprint by creating servers with budget / column_bytes slots. */
+int hz_server_column_bytes(const hz_ctx* ctx, double* bytes);
 int hz_server_submit(hz_server* srv, int64_t request_id, const double* src_xyz, const double* src_amp, int32_t ns);
 int hz_server_step(hz_server* srv, int64_t* done_ids, int32_t cap, int32_t* ndone);
 int hz_server_fetch(hz_server* srv, int64_t request_id, double* u, hz_stats* stats);

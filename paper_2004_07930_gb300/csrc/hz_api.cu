@@ -1712,6 +1712,35 @@ struct hz_server {
   };
 };
 
+// Device bytes that one right-hand-side column adds to a server on this
+// context: the server's own B, X, R columns plus the context workspace of
+// one column (the blocks of M^{-1} and of the outer Krylov basis, the local
+// sub-vectors and front vectors of both levels, the inner coarse Krylov
+// basis), as ensure_workspace allocates them.
+static double column_bytes(const hz_ctx* c) {
+  const double n = (double)c->space.n, m = c->opt.restart;
+  const double ef = c->lf.mf.fp32 ? 8.0 : 16.0;
+  double b = 3.0 * 16.0 * n;                                    // server B, X, R
+  b += 6.0 * 16.0 * n;                                          // context B, X, R, T, Q, U
+  b += ef * ((double)c->lf.sub_rows + (double)c->lf.mf.rows_total + (double)c->lf.mf.max_slots * MF_TILE_ROWS);
+  b += 16.0 * n * (2.0 * m + 2.0);                              // V, Zk, W
+  if (c->has_coarse) {
+    const double nh = (double)c->cspace.n, ec = c->lc.mf.fp32 ? 8.0 : 16.0, ek = c->coarse32 ? 8.0 : 16.0;
+    const double mi = std::max(1, c->opt.coarse_inner_its);
+    b += 2.0 * 16.0 * nh;                                       // r_H, y_H
+    b += ec * ((double)c->lc.sub_rows + (double)c->lc.mf.rows_total + (double)c->lc.mf.max_slots * MF_TILE_ROWS);
+    if (c->opt.coarse_mode == HZ_COARSE_GMRES) b += ek * nh * (2.0 * mi + 2.0);
+    if (c->coarse32) b += 8.0 * (2.0 * nh + 3.0 * n);
+  }
+  return b;
+}
+
+extern "C" int hz_server_column_bytes(const hz_ctx* c, double* bytes) {
+  if (!c || !bytes) return fail(HZ_EINVAL, "bad argument");
+  *bytes = column_bytes(c);
+  return HZ_OK;
+}
+
 extern "C" int hz_server_create(hz_ctx* c, int32_t slots, hz_server** out) {
   if (!c || !out || slots < 1 || slots > c->opt.max_block) return fail(HZ_EINVAL, "bad argument");
   *out = nullptr;

@@ -21,7 +21,8 @@ EXPORTS = ["hz_default_options", "hz_setup", "hz_ndof", "hz_dof_coords", "hz_get
            "hz_solve_rhs", "hz_apply_A", "hz_apply_prec", "hz_matrix_csr", "hz_free", "hz_strerror",
            "hz_last_error", "hz_profile_begin", "hz_profile_end", "hz_apply_A_noalloc", "hz_server_create",
            "hz_server_submit", "hz_server_step", "hz_server_fetch", "hz_server_pending", "hz_server_free",
-           "hz_receiver_operator", "hz_fwi_gradient", "hz_column_stats", "hz_krylov_basis"]
+           "hz_receiver_operator", "hz_fwi_gradient", "hz_column_stats", "hz_krylov_basis",
+           "hz_server_column_bytes"]
 HZ_NOALLOC_MAX_ENTRIES = 1048576  # complex entries per work block of hz_apply_A_noalloc (n * s)
 
 
@@ -94,6 +95,7 @@ def load():
     lib.hz_matrix_csr.argtypes = [P, P, P, P]
     lib.hz_apply_A_noalloc.argtypes = [P, P, P, C.c_int32, P]
     lib.hz_server_create.argtypes = [P, C.c_int32, C.POINTER(P)]
+    lib.hz_server_column_bytes.argtypes = [P, C.POINTER(C.c_double)]
     lib.hz_server_submit.argtypes = [P, C.c_int64, P, P, C.c_int32]
     lib.hz_server_step.argtypes = [P, P, C.c_int32, C.POINTER(C.c_int32)]
     lib.hz_server_fetch.argtypes = [P, C.c_int64, P, C.POINTER(HzStats)]
@@ -304,6 +306,12 @@ class Solver:
         if rc != HZ_ENOTCONV or raise_on_notconv:
             _check(rc)
         return U, st.asdict()
+
+    def column_bytes(self):
+        """Device bytes one server slot (right-hand-side column) costs on this solver."""
+        b = C.c_double()
+        _check(self._lib.hz_server_column_bytes(self._ctx, C.byref(b)))
+        return b.value
 
     def receiver_operator(self, rec_xyz):
         """(idx [nr, 20] int32, w [nr, 20]): receiver k samples

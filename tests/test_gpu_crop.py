@@ -8,8 +8,11 @@ and boundary conditions; it is split into 4 box subdomains with the nested
 surface sources are compared element by element (dofs matched by
 coordinates) with the oracle's direct solve:
 
-* FP64 form at GMRES rtol 1e-6: relative L2 <= 1e-6, and <= 1e-8 at rtol
-  1e-10;
+* FP64 form: relative L2 <= 1e-6 at GMRES rtol 1e-7, and <= 1e-8 at rtol
+  1e-10. The rtol is a residual bound: on this crop the forward error at
+  rtol 1e-6 equals the residual to within a few per mille (1.00009e-6 was
+  measured for one of the two sources), so the 1e-6 wavefield bound is
+  checked one decade tighter, and rtol 1e-6 is held to 2e-6;
 * mixed form (complex FP32 local solves) at rtol 1e-6: <= 1e-5, with the
   coarse level in FP64 (default) and in FP32 (coarse_fp32 = 1).
 """
@@ -36,7 +39,8 @@ def crop():
 
 
 @pytest.mark.parametrize("precision,coarse_fp32,rtol,bound", [
-    (hz.HZ_PREC_FP64, 0, 1e-6, 1e-6),
+    (hz.HZ_PREC_FP64, 0, 1e-6, 2e-6),
+    (hz.HZ_PREC_FP64, 0, 1e-7, 1e-6),
     (hz.HZ_PREC_FP64, 0, 1e-10, 1e-8),
     (hz.HZ_PREC_MIXED, 0, 1e-6, 1e-5),
     (hz.HZ_PREC_MIXED, 1, 1e-6, 1e-5),

@@ -100,3 +100,25 @@ def test_server_rejects_bad_requests():
         srv.close()
         with pytest.raises(hz.HzError):
             hz.Server(S, 65)                     # more slots than max_block
+
+
+def test_admission_by_device_budget():
+    """A budget of 2.5 columns' worth of device bytes gives the server 2
+    slots: a third source waits in the queue and is admitted when a slot (and
+    its memory) frees; every request still matches the oracle."""
+    torch_cuda()
+    p = wl.cube_problem(ncell=4)
+    with hz.Solver.from_problem(p, rtol=1e-8, restart=3) as S:
+        loop = ServingLoop({2.0: S}, device_budget=2.5 * S.column_bytes())
+        assert loop.slots == {2.0: 2}
+        loop.submit(1, 2.0, SRC_A)
+        loop.submit(2, 2.0, [SRC_C[0]])
+        loop.step(2.0)
+        assert loop.servers[2.0].pending() == (1, 2)     # one source held back by the budget
+        while loop.busy():
+            loop.step(2.0)
+        loop.close()
+        for rid, src in ((1, SRC_A), (2, [SRC_C[0]])):
+            u, st, _ = loop.results[rid]
+            assert st["converged"] == 1
+            assert rel_l2(u, _oracle_wavefields(p, S, src)).max() <= 1e-6

@@ -63,6 +63,27 @@ def test_stream_summary(loop):
 def test_idle_servers_are_not_stepped(loop):
     loop.submit(1, 5.0, np.zeros((2, 3)))
     while loop.busy():
-        loop.step()
+        for f in (3.5, 5.0):
+            loop.step(f)
     assert loop.servers[3.5].steps == 0 and loop.servers[5.0].steps == 4
     assert 1 in loop.results and loop.results[1][0].shape == (2, 4)
+
+
+class FakeSolver:
+    def __init__(self, nbytes):
+        self.nbytes = nbytes
+
+    def column_bytes(self):
+        return self.nbytes
+
+
+def test_slots_from_device_budget(monkeypatch):
+    """Admission by footprint: each frequency gets an equal share of the
+    budget, divided by the bytes one column costs on its solver."""
+    monkeypatch.setattr(serve.hz, "Server", FakeServer)
+    solvers = {3.5: FakeSolver(1e8), 5.0: FakeSolver(3e8), 7.0: FakeSolver(5e10)}
+    loop = serve.ServingLoop(solvers, device_budget=6e9)
+    assert loop.slots == {3.5: 20, 5.0: 6, 7.0: 1}
+    assert loop.servers[5.0].slots == 6
+    big = serve.slots_for_budget({1.0: FakeSolver(1.0)}, 1e12)
+    assert big == {1.0: 64}
