@@ -124,6 +124,8 @@ def parse():
                     help="coarse level of the headline forms (the paper's: gmres, 10 inner steps)")
     ap.add_argument("--tensor-cores", type=int, choices=[-1, 0, 1], default=-1,
                     help="mixed form: front sweeps on the tcgen05 tensor cores (1) or SIMT (0); -1: library default")
+    ap.add_argument("--persistent", type=int, choices=[-1, 0, 1], default=-1,
+                    help="SIMT front sweeps as one launch per direction (1) or one per level (0); -1: library default")
     ap.add_argument("--spmm-sweep", action="store_true",
                     help="instead of the throughput line: HBM and FP64 rates of the product with A "
                          "(hz_apply_A, device blocks) for block widths 1..16 on the bench workload")
@@ -340,6 +342,8 @@ def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, ser
     prec = hz.HZ_PREC_MIXED if form == "mixed" else hz.HZ_PREC_FP64
     if TENSOR_CORES >= 0:
         opts["tensor_cores"] = TENSOR_CORES
+    if PERSISTENT >= 0:
+        opts["persistent_sweeps"] = PERSISTENT
     t0 = time.time()
     S = hz.Solver.from_problem(prob, precision=prec, rtol=1e-6, stream=stream, maxit=MAXIT, **opts)
     setup_wall = time.time() - t0
@@ -374,7 +378,8 @@ def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, ser
            "iterations": [s["iterations"] for s in stats], "max_rel_residual": max(s["max_rel_residual"] for s in stats),
            "converged": all(s["converged"] for s in stats), "setup_s": setup_wall,
            "factor_s": stats[0]["factor_seconds"], "info": info, "phases": prof, "gpu_launches": launches,
-           "coarse_fp32": S.options.coarse_fp32, "overlap": S.options.overlap}
+           "coarse_fp32": S.options.coarse_fp32, "overlap": S.options.overlap,
+           "tensor_cores": S.options.tensor_cores, "persistent_sweeps": S.options.persistent_sweeps}
     if with_e2e:
         import numpy as np
 
@@ -399,6 +404,7 @@ def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, ser
 
 MAXIT = 500
 TENSOR_CORES = -1
+PERSISTENT = -1
 
 
 def run_spmm_sweep(args):
@@ -500,10 +506,11 @@ def run_serving(args):
 
 
 def main():
-    global MAXIT, TENSOR_CORES
+    global MAXIT, TENSOR_CORES, PERSISTENT
     args = parse()
     MAXIT = args.maxit
     TENSOR_CORES = args.tensor_cores
+    PERSISTENT = args.persistent
     if args.impl == "reference":
         run_reference(args)
         return
@@ -568,8 +575,10 @@ def main():
     flops_achieved = ph["flops"] / (ph["ms"] / 1e3) / 1e12
     tc_on = (TENSOR_CORES if TENSOR_CORES >= 0 else hz.default_options().tensor_cores) == 1
     if head == "mixed":
-        kern = ("fine local solves (tcgen05 sweep tiles, 3xTF32 split, FP32 accumulation in TMEM)" if tc_on else
-                "fine local solves (SIMT complex FP32 sweep tiles)")
+        pers = r.get("persistent_sweeps", 0) == 1
+        kern = ("fine local solves (tcgen05 sweep tiles, 3xTF32 split, FP32 accumulation in TMEM, one launch per "
+                "level)" if tc_on else "fine local solves (SIMT complex FP32 sweep tiles, %s)" %
+                ("k_mf_sweep: one launch per sweep over all levels" if pers else "k_mf_tile + k_mf_reduce per level"))
         # a sweep reads each factor entry once per application: HBM is the roof of the
         # tensor-core form; the SIMT FP32 rate (16 flops per factor byte at s = 16) is given beside it
         roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm, "unit": "GB/s", "frac": hbm_achieved / hbm,

@@ -99,14 +99,14 @@ constexpr int MF_TILE_ROWS = 128;  // output rows per sweep tile (MF_TILE in mf.
 constexpr int MF_TILE_K = 128;     // reduction length per sweep tile (MF_TK in mf.cu)
 
 void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const FrontTree*>& trees,
-              const std::vector<int64_t>& sub_off, bool fp32, bool tc, DevMF& mf, MFHost& info, DevPool& pool,
-              cudaStream_t st) {
+              const std::vector<int64_t>& sub_off, bool fp32, bool tc, bool persistent, DevMF& mf, MFHost& info,
+              DevPool& pool, cudaStream_t st) {
   tc = tc && fp32;
   const size_t ns = mats.size();
   std::vector<int> base(ns + 1, 0);
   for (size_t i = 0; i < ns; ++i) base[i + 1] = base[i] + (int)trees[i]->k.size();
   const int nf = base[ns];
-  std::vector<int> k(nf), f(nf), height(nf), child_ptr(nf + 1, 0), child_idx;
+  std::vector<int> k(nf), f(nf), height(nf), child_ptr(nf + 1, 0), child_idx, parent(nf, -1);
   std::vector<int64_t> Foff(nf + 1, 0), rowoff(nf + 1, 0), Moff(nf + 1, 0), Doff(nf + 1, 0);
   for (size_t i = 0; i < ns; ++i) {
     const FrontTree& T = *trees[i];
@@ -115,6 +115,7 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
       k[g] = T.k[t];
       f[g] = T.k[t] + T.m[t];
       height[g] = T.height[t];
+      parent[g] = T.parent[t] >= 0 ? base[i] + T.parent[t] : -1;
       info.factor_entries += (int64_t)T.k[t] * (T.k[t] + 1) / 2 + (int64_t)T.k[t] * T.m[t];
     }
   }
@@ -334,6 +335,71 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
   mf.brb_ptr_h = info.brb_ptr.data();
   mf.level_row_h = info.level_row.data();
   mf.max_slots = max_slots;
+  if (persistent) {
+    // the same tiles renumbered for one launch per sweep: slots unique over all levels, the
+    // backward tiles ordered from the roots down
+    std::vector<int4> ptf, ptb, prbf, prbb;
+    std::vector<int> srf, srb, nrbf(nf, 0), nrbb(nf, 0), nch(nf);
+    for (int g = 0; g < nf; ++g) nch[g] = child_ptr[g + 1] - child_ptr[g];
+    auto renumber = [&](const std::vector<int4>& tl, const std::vector<int>& tptr, bool fwd, std::vector<int4>& out,
+                        std::vector<int4>& rbs, std::vector<int>& slot_rb, std::vector<int>& nrb) {
+      for (int li = 0; li <= maxh; ++li) {
+        const int l = fwd ? li : maxh - li;
+        // within a level, tiles of one row block are adjacent (built that way above)
+        for (int q = tptr[l]; q < tptr[l + 1]; ++q) {
+          int4 t = tl[q];
+          if (t.w < 0) {
+            out.push_back(t);
+            nrb[t.x]++;
+            continue;
+          }
+          const bool first = out.empty() || out.back().w < 0 || out.back().x != t.x || out.back().y != t.y;
+          if (first) {
+            rbs.push_back(make_int4(t.x, t.y, 0, (int)slot_rb.size()));
+            nrb[t.x]++;
+          }
+          rbs.back().z++;
+          t.w = (int)slot_rb.size();
+          slot_rb.push_back((int)rbs.size() - 1);
+          out.push_back(t);
+        }
+      }
+    };
+    renumber(ftiles, info.ftile_ptr, true, ptf, prbf, srf, nrbf);
+    renumber(btiles, info.btile_ptr, false, ptb, prbb, srb, nrbb);
+    // forward: a front waits for its children that have rows (a child without rows has no update
+    // rows either and contributes nothing); backward: a front waits for its nearest ancestor with
+    // pivots, which finishes only after all of its own ancestors
+    std::vector<int> bdep(nf, -1);
+    for (int g = 0; g < nf; ++g) {
+      nch[g] = 0;
+      for (int q = child_ptr[g]; q < child_ptr[g + 1]; ++q) nch[g] += nrbf[child_idx[q]] > 0;
+      int a = parent[g];
+      while (a >= 0 && nrbb[a] == 0) a = parent[a];
+      bdep[g] = a;
+    }
+    mf.persistent = 1;
+    mf.pt_nf = (int)ptf.size();
+    mf.pt_nb = (int)ptb.size();
+    mf.prb_nf = (int)prbf.size();
+    mf.prb_nb = (int)prbb.size();
+    mf.ptf = pool.upload(ptf, st);
+    mf.ptb = pool.upload(ptb, st);
+    mf.slot_rb_f = pool.upload(srf, st);
+    mf.slot_rb_b = pool.upload(srb, st);
+    mf.prb_f = pool.upload(prbf, st);
+    mf.prb_b = pool.upload(prbb, st);
+    mf.nrb_f = pool.upload(nrbf, st);
+    mf.nrb_b = pool.upload(nrbb, st);
+    mf.parent = pool.upload(parent, st);
+    mf.bdep = pool.upload(bdep, st);
+    mf.nchild = pool.upload(nch, st);
+    mf.cnt_n = 1 + std::max(mf.prb_nf, mf.prb_nb) + 2 * nf;
+    mf.cnt = pool.alloc<int>(mf.cnt_n);
+    mf.pslots = std::max<int64_t>(1, std::max(srf.size(), srb.size()));
+    mf.sw_err = pool.alloc<int>(1);
+    CK(cudaMemsetAsync(mf.sw_err, 0, sizeof(int), st));
+  }
   mf.frb = pool.upload(frb, st);
   mf.brb = pool.upload(brb, st);
   mf.row_front = pool.upload(row_front, st);
@@ -452,8 +518,8 @@ struct LevelDev {             // one level of ORAS on the device
   double amax = 0.0;
 };
 
-void build_level(const Space& sp, const std::vector<Subdomain>& subs, int leaf, bool fp32, bool tc, LevelDev& L,
-                 DevPool& pool, cudaStream_t st) {
+void build_level(const Space& sp, const std::vector<Subdomain>& subs, int leaf, bool fp32, bool tc, bool persistent,
+                 LevelDev& L, DevPool& pool, cudaStream_t st) {
   const size_t np = subs.size();
   std::vector<int64_t> sub_off(np + 1, 0);
   for (size_t i = 0; i < np; ++i) sub_off[i + 1] = sub_off[i] + (int64_t)subs[i].dofs.size();
@@ -475,7 +541,7 @@ void build_level(const Space& sp, const std::vector<Subdomain>& subs, int leaf, 
     tr[i] = &L.trees[i];
     for (const cplx& v : subs[i].A.val) L.amax = std::max(L.amax, std::abs(v));
   }
-  build_mf(mats, tr, sub_off, fp32, tc, L.mf, L.info, pool, st);
+  build_mf(mats, tr, sub_off, fp32, tc, persistent, L.mf, L.info, pool, st);
   std::vector<int> gidx(sub_off[np]), own(sp.n, -1);
   for (size_t i = 0; i < np; ++i)
     for (size_t l = 0; l < subs[i].dofs.size(); ++l) {
@@ -490,14 +556,14 @@ void build_level(const Space& sp, const std::vector<Subdomain>& subs, int leaf, 
 }
 
 // A single "subdomain" covering the whole matrix: direct factorisation.
-void build_direct(const Space& sp, const CsrC& A, int leaf, bool fp32, bool tc, LevelDev& L, DevPool& pool,
-                  cudaStream_t st) {
+void build_direct(const Space& sp, const CsrC& A, int leaf, bool fp32, bool tc, bool persistent, LevelDev& L,
+                  DevPool& pool, cudaStream_t st) {
   std::vector<Subdomain> one(1);
   one[0].dofs.resize(sp.n);
   std::iota(one[0].dofs.begin(), one[0].dofs.end(), 0);
   one[0].owned.assign(sp.n, 1);
   one[0].A = A;
-  build_level(sp, one, leaf, fp32, tc, L, pool, st);
+  build_level(sp, one, leaf, fp32, tc, persistent, L, pool, st);
 }
 
 void mesh_from_abi(const hz_mesh* in, Mesh& m) {
@@ -678,7 +744,7 @@ void ensure_workspace(hz_ctx* c, int s) {
   const size_t ef = c->lf.mf.fp32 ? sizeof(float2) : sizeof(double2);
   c->Xsub = (double2*)p.alloc<char>(c->lf.sub_rows * s * ef);
   c->lf.mf.Wout = p.alloc<char>(c->lf.mf.rows_total * s * ef);
-  c->lf.mf.P = p.alloc<char>((size_t)c->lf.mf.max_slots * MF_TILE_ROWS * s * ef);
+  c->lf.mf.P = p.alloc<char>((size_t)std::max(c->lf.mf.max_slots, c->lf.mf.pslots) * MF_TILE_ROWS * s * ef);
   c->lf.mf.s_cap = s;
   alloc_krylov(c->Kout, n, s, c->opt.restart, p, false);
   if (c->opt.block_arnoldi) {
@@ -715,7 +781,7 @@ void ensure_workspace(hz_ctx* c, int s) {
     const size_t ec = c->lc.mf.fp32 ? sizeof(float2) : sizeof(double2);
     c->XsubH = (double2*)p.alloc<char>(c->lc.sub_rows * s * ec);
     c->lc.mf.Wout = p.alloc<char>(c->lc.mf.rows_total * s * ec);
-    c->lc.mf.P = p.alloc<char>((size_t)c->lc.mf.max_slots * MF_TILE_ROWS * s * ec);
+    c->lc.mf.P = p.alloc<char>((size_t)std::max(c->lc.mf.max_slots, c->lc.mf.pslots) * MF_TILE_ROWS * s * ec);
     c->lc.mf.s_cap = s;
     if (c->opt.coarse_mode == HZ_COARSE_GMRES) {
       alloc_krylov(c->Kin, nh, s, std::max(1, c->opt.coarse_inner_its), p, c->coarse32);
@@ -1069,16 +1135,18 @@ int fgmres(hz_ctx* c, int s, hz_stats* stats) {
 // which it happened and does not fail later calls.
 void check_sweep_flags(hz_ctx* c) {
   for (DevMF* mf : {&c->lf.mf, &c->lc.mf})
-    if (mf->tc_err) {
-      int e = 0;
-      CK(cudaMemcpyAsync(&e, mf->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-      CK(cudaStreamSynchronize(c->st));
-      if (e) {
-        CK(cudaMemsetAsync(mf->tc_err, 0, sizeof(int), c->st));
+    for (int* flag : {mf->tc_err, mf->sw_err})
+      if (flag) {
+        int e = 0;
+        CK(cudaMemcpyAsync(&e, flag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
         CK(cudaStreamSynchronize(c->st));
-        throw HzError{HZ_EINTERNAL, "tensor-core sweep tile timed out on a barrier"};
+        if (e) {
+          CK(cudaMemsetAsync(flag, 0, sizeof(int), c->st));
+          CK(cudaStreamSynchronize(c->st));
+          throw HzError{HZ_EINTERNAL, flag == mf->tc_err ? "tensor-core sweep tile timed out on a barrier"
+                                                         : "persistent front sweep timed out on a dependency"};
+        }
       }
-    }
 }
 
 int fail(int code, const std::string& msg) {
@@ -1185,6 +1253,7 @@ int hz_default_options(hz_options* o) {
   o->coarse_fp32 = 0;
   o->debug_bounds = 0;
   o->block_arnoldi = 0;
+  o->persistent_sweeps = 1;
   return HZ_OK;
 }
 
@@ -1243,7 +1312,8 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
     upload_split(c->A_host, c->A, c->pool, c->st, mixed);
     std::vector<Subdomain> subs = build_subdomains(c->fine, c->space, part, nparts, mvals, omega, o.overlap);
     const bool tc = mixed && o.tensor_cores != 0;
-    build_level(c->space, subs, o.leaf_size, mixed, tc, c->lf, c->pool, c->st);
+    const bool pers = o.persistent_sweeps != 0;
+    build_level(c->space, subs, o.leaf_size, mixed, tc, pers, c->lf, c->pool, c->st);
     subs.clear();
     if (o.coarse_mode != HZ_COARSE_NONE) {
       c->has_coarse = true;
@@ -1261,9 +1331,9 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
       if (o.coarse_mode == HZ_COARSE_GMRES) {
         std::vector<Subdomain> csubs =
             build_subdomains(c->coarse, c->cspace, C.part, nparts, C.mvals, omega, o.overlap);
-        build_level(c->cspace, csubs, o.leaf_size, mixed, tc, c->lc, c->pool, c->st);
+        build_level(c->cspace, csubs, o.leaf_size, mixed, tc, pers, c->lc, c->pool, c->st);
       } else {
-        build_direct(c->cspace, C.E, o.leaf_size, mixed, tc, c->lc, c->pool, c->st);
+        build_direct(c->cspace, C.E, o.leaf_size, mixed, tc, pers, c->lc, c->pool, c->st);
       }
     }
     CK(cudaStreamSynchronize(c->st));

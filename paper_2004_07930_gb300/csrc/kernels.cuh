@@ -97,6 +97,28 @@ struct DevMF {
   int* tc_err = nullptr;        // device flag: a tensor-core tile gave up waiting on a barrier
   cudaStream_t side = nullptr;  // tensor-core mode: the SIMT tiles of a level run here, beside the tcgen05 tiles
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // persistent sweeps (one launch per direction): tiles in ticket order with slots numbered over all
+  // levels, row blocks (front, first row, tiles, first slot), slot -> row block, per-front row-block
+  // counts, parent and child counts, and the counters reset before every sweep
+  int persistent = 0;
+  int pt_nf = 0, pt_nb = 0;     // tiles of the forward / backward sweep
+  int prb_nf = 0, prb_nb = 0;   // row blocks with partial tiles
+  int4* ptf = nullptr;          // forward tiles, leaves first
+  int4* ptb = nullptr;          // backward tiles, roots first
+  int* slot_rb_f = nullptr;
+  int* slot_rb_b = nullptr;
+  int4* prb_f = nullptr;
+  int4* prb_b = nullptr;
+  int* nrb_f = nullptr;         // [nfronts] row blocks of each front, forward
+  int* nrb_b = nullptr;         // [nfronts] backward
+  int* parent = nullptr;        // [nfronts] parent front (-1: root)
+  int* bdep = nullptr;          // [nfronts] nearest ancestor with pivots (-1: none): backward dependency
+  int* nchild = nullptr;        // [nfronts]
+  int* cnt = nullptr;           // ticket | row-block counts | front counts | ready children
+  int cnt_n = 0;
+  int64_t pslots = 0;           // partial slots of the larger sweep
+  int* sw_err = nullptr;        // device flag: a persistent sweep gave up waiting
+  int sweep_grid = 0;           // resident CTAs of the sweep kernel
 };
 
 // tensor-core tile eligibility (output rows, reduction length) and packing geometry

@@ -284,25 +284,33 @@ static constexpr size_t tile_smem_bytes() {
   return sizeof(V) * ((size_t)MF_TK * S + 2 * (size_t)TileChunk<V>::K * MF_TILE);
 }
 
-// Each thread owns one output row (MF_TILE threads) and keeps the s
+// loads of data that other CTAs of the same launch write (persistent sweeps):
+// through L2 only, so that no stale line of this SM's L1 is read
+template <bool CG, typename V>
+__device__ __forceinline__ V ldv(const V* p) {
+  if constexpr (CG)
+    return __ldcg(p);
+  else
+    return *p;
+}
+
+// One tile. Each thread owns one output row (MF_TILE threads) and keeps the s
 // right-hand sides as register accumulators. The tile's input rows are
 // staged once in shared memory (read as broadcasts); the factor tile streams
 // through a two-chunk shared-memory ring filled by cp.async (a warp copies 32
 // consecutive entries of one factor column), so the next chunk's loads are in
-// flight while the current one is consumed.
-template <typename V, int S, bool FWD>
-__global__ void __launch_bounds__(MF_TILE) k_mf_tile(const int4* __restrict__ tiles, const int* __restrict__ kk,
-                                                     const int* __restrict__ ff, const int64_t* __restrict__ rowoff,
-                                                     const int64_t* __restrict__ Moff, const V* __restrict__ M,
-                                                     const int* __restrict__ rows, const int64_t* __restrict__ cptr,
-                                                     const int* __restrict__ cidx, const int64_t* __restrict__ Doff,
-                                                     const V* __restrict__ Dinv, V* __restrict__ Xsub,
-                                                     V* __restrict__ Wout, V* __restrict__ P, int s) {
+// flight while the current one is consumed. A tile with slot >= 0 writes its
+// partial result to P; the others apply the epilogue.
+template <typename V, int S, bool FWD, bool CG>
+__device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restrict__ kk, const int* __restrict__ ff,
+                                           const int64_t* __restrict__ rowoff, const int64_t* __restrict__ Moff,
+                                           const V* __restrict__ M, const int* __restrict__ rows,
+                                           const int64_t* __restrict__ cptr, const int* __restrict__ cidx,
+                                           const int64_t* __restrict__ Doff, const V* __restrict__ Dinv, V* Xsub,
+                                           V* Wout, V* P, int s, unsigned char* smem_raw) {
   constexpr int KCH = TileChunk<V>::K;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   V(*bs)[S] = reinterpret_cast<V(*)[S]>(smem_raw);                                       // [MF_TK][S]
   V(*mb)[MF_TILE] = reinterpret_cast<V(*)[MF_TILE]>(smem_raw + sizeof(V) * MF_TK * S);  // [2 KCH][MF_TILE]
-  const int4 tile = tiles[blockIdx.x];
   const int t = tile.x, r0 = tile.y, c0 = tile.z, slot = tile.w;
   const int f = ff[t], k = kk[t];
   const int nout = FWD ? f : k;
@@ -331,14 +339,14 @@ __global__ void __launch_bounds__(MF_TILE) k_mf_tile(const int4* __restrict__ ti
     V v[S];
     const V* src = (FWD || local >= k) ? Xsub + (int64_t)rows[R] * s : Wout + R * s;
 #pragma unroll
-    for (int c = 0; c < S; ++c) v[c] = c < s ? src[c] : mk2((decltype(V::x))0, (decltype(V::x))0);
+    for (int c = 0; c < S; ++c) v[c] = c < s ? ldv<CG>(src + c) : mk2((decltype(V::x))0, (decltype(V::x))0);
     if (FWD) {
       const int64_t pe = cptr[R + 1];
       for (int64_t p = cptr[R]; p < pe; ++p) {
         const V* w = Wout + (int64_t)cidx[p] * s;
 #pragma unroll
         for (int c = 0; c < S; ++c)
-          if (c < s) v[c] = c_add(v[c], w[c]);
+          if (c < s) v[c] = c_add(v[c], ldv<CG>(w + c));
       }
     }
 #pragma unroll
@@ -392,7 +400,7 @@ __global__ void __launch_bounds__(MF_TILE) k_mf_tile(const int4* __restrict__ ti
         const V* w = Wout + (int64_t)cidx[p] * s;
 #pragma unroll
         for (int c = 0; c < S; ++c)
-          if (c < s) acc[c] = c_add(acc[c], w[c]);
+          if (c < s) acc[c] = c_add(acc[c], ldv<CG>(w + c));
       }
 #pragma unroll
       for (int c = 0; c < S; ++c)
@@ -406,12 +414,52 @@ __global__ void __launch_bounds__(MF_TILE) k_mf_tile(const int4* __restrict__ ti
   }
 }
 
-// Row-block epilogue, one thread per (row, column): sum the row block's
-// partial tiles in order, then
+template <typename V, int S, bool FWD>
+__global__ void __launch_bounds__(MF_TILE) k_mf_tile(const int4* __restrict__ tiles, const int* __restrict__ kk,
+                                                     const int* __restrict__ ff, const int64_t* __restrict__ rowoff,
+                                                     const int64_t* __restrict__ Moff, const V* __restrict__ M,
+                                                     const int* __restrict__ rows, const int64_t* __restrict__ cptr,
+                                                     const int* __restrict__ cidx, const int64_t* __restrict__ Doff,
+                                                     const V* __restrict__ Dinv, V* __restrict__ Xsub,
+                                                     V* __restrict__ Wout, V* __restrict__ P, int s) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  sweep_tile<V, S, FWD, false>(tiles[blockIdx.x], kk, ff, rowoff, Moff, M, rows, cptr, cidx, Doff, Dinv, Xsub, Wout,
+                               P, s, smem_raw);
+}
+
+// Epilogue of a split row block (rb = front, first row, tiles, first slot):
+// sum its partial tiles in slot order, then
 //   forward : rows r < k -> y = t / D (kept in Wout for the backward sweep);
 //             rows r >= k -> parent update c_U + t (Wout), c_U = the children's
 //             update vectors landing on the row
 //   backward: x at the pivot rows of the sub-vector
+// (i, c) = (row of the block, column); CG: partials and update vectors
+// written by other CTAs of the same launch are read through L2
+template <typename V, bool FWD, bool CG>
+__device__ __forceinline__ void rb_epilogue(const int4 rb, int i, int c, const int* __restrict__ kk,
+                                            const int* __restrict__ ff, const int64_t* __restrict__ rowoff,
+                                            const int64_t* __restrict__ Doff, const int* __restrict__ rows,
+                                            const int64_t* __restrict__ cptr, const int* __restrict__ cidx,
+                                            const V* __restrict__ Dinv, V* Wout, const V* P, V* Xsub, int s) {
+  const int t = rb.x, r = rb.y + i;
+  const int k = kk[t];
+  if (r >= (FWD ? ff[t] : k)) return;
+  V acc = mk2((decltype(V::x))0, (decltype(V::x))0);
+  for (int q = 0; q < rb.z; ++q) acc = c_add(acc, ldv<CG>(P + ((int64_t)(rb.w + q) * MF_TILE + i) * s + c));
+  const int64_t R = rowoff[t] + r;
+  if (FWD) {
+    if (r < k) {
+      Wout[R * s + c] = c_mul(acc, Dinv[Doff[t] + r]);
+    } else {
+      for (int64_t p = cptr[R]; p < cptr[R + 1]; ++p) acc = c_add(acc, ldv<CG>(Wout + (int64_t)cidx[p] * s + c));
+      Wout[R * s + c] = acc;
+    }
+  } else {
+    Xsub[(int64_t)rows[R] * s + c] = acc;
+  }
+}
+
+// Row-block epilogues of one level, one thread per (row, column).
 template <typename V, bool FWD>
 __global__ void k_mf_reduce(const int4* __restrict__ rblocks, int nrb, const int* __restrict__ kk,
                             const int* __restrict__ ff, const int64_t* __restrict__ rowoff,
@@ -422,23 +470,127 @@ __global__ void k_mf_reduce(const int4* __restrict__ rblocks, int nrb, const int
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t per = (int64_t)MF_TILE * s;
   if (g >= nrb * per) return;
-  const int4 rb = rblocks[g / per];
   const int i = (int)((g % per) / s), c = (int)(g % s);
-  const int t = rb.x, r = rb.y + i;
-  const int k = kk[t];
-  if (r >= (FWD ? ff[t] : k)) return;
-  V acc = mk2((decltype(V::x))0, (decltype(V::x))0);
-  for (int q = 0; q < rb.z; ++q) acc = c_add(acc, P[((int64_t)(rb.w + q) * MF_TILE + i) * s + c]);
-  const int64_t R = rowoff[t] + r;
-  if (FWD) {
-    if (r < k) {
-      Wout[R * s + c] = c_mul(acc, Dinv[Doff[t] + r]);
-    } else {
-      for (int64_t p = cptr[R]; p < cptr[R + 1]; ++p) acc = c_add(acc, Wout[(int64_t)cidx[p] * s + c]);
-      Wout[R * s + c] = acc;
+  rb_epilogue<V, FWD, false>(rblocks[g / per], i, c, kk, ff, rowoff, Doff, rows, cptr, cidx, Dinv, Wout, P, Xsub, s);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent sweeps: one launch per sweep direction over every level.
+//
+// Resident CTAs take the tiles in level order through a ticket counter (the
+// forward sweep from the leaves up, the backward sweep from the roots down).
+// Before its tile, a CTA waits until the front's inputs are final: forward,
+// every child front with rows has finished (its parent-update rows written);
+// backward, the nearest ancestor with pivots has finished (so all the
+// ancestors' pivots are final in the sub-vector; `parent` is that ancestor
+// in the backward launch). A split row block's partial tiles count themselves in; the
+// last one sums the partials in slot order (so the result does not depend
+// on which tile comes last) and applies the epilogue. A front has finished
+// when all its row blocks have, and then (forward) it counts itself into its
+// parent. Every dependency has a smaller ticket, and a ticket is only taken
+// by a running CTA, so the smallest unfinished ticket can always proceed.
+// Waits are bounded by the global timer; a timeout sets *err and the CTA
+// stops taking tiles (the sweep's result is then invalid and reported).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t sw_clock_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ int sw_load(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// wait until *p >= target; false after about two seconds
+__device__ __forceinline__ bool sw_wait(const int* p, int target) {
+  if (sw_load(p) >= target) return true;
+  const uint64_t t0 = sw_clock_ns();
+  while (sw_load(p) < target) {
+    __nanosleep(200);
+    if (sw_clock_ns() - t0 > 2000000000ull) return false;
+  }
+  return true;
+}
+
+template <typename V, int S, bool FWD>
+__global__ void __launch_bounds__(MF_TILE) k_mf_sweep(
+    const int4* __restrict__ tiles, int ntiles, const int* __restrict__ slot_rb, const int4* __restrict__ rblocks,
+    const int* __restrict__ front_nrb, const int* __restrict__ parent, const int* __restrict__ nchild,
+    int* __restrict__ cnt, int nrb_total, int nfronts, int* __restrict__ err, const int* __restrict__ kk,
+    const int* __restrict__ ff, const int64_t* __restrict__ rowoff, const int64_t* __restrict__ Moff,
+    const V* __restrict__ M, const int* __restrict__ rows, const int64_t* __restrict__ cptr,
+    const int* __restrict__ cidx, const int64_t* __restrict__ Doff, const V* __restrict__ Dinv, V* Xsub, V* Wout,
+    V* P, int s) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_tile, s_flag;
+  int* ticket = cnt;
+  int* rb_cnt = cnt + 1;
+  int* front_done = rb_cnt + nrb_total;
+  int* child_ready = front_done + nfronts;
+  const int tid = threadIdx.x;
+  while (true) {
+    if (tid == 0) {
+      int tk = atomicAdd(ticket, 1);
+      const int4 tl = tk < ntiles ? tiles[tk] : make_int4(0, 0, 0, 0);
+      bool ok = true;
+      if (tk < ntiles) {
+        const int g = tl.x;
+        if (FWD) {
+          ok = sw_wait(child_ready + g, nchild[g]);
+        } else if (parent[g] >= 0) {
+          ok = sw_wait(front_done + parent[g], front_nrb[parent[g]]);
+        }
+        if (!ok) {
+          atomicExch(err, 1);
+          tk = ntiles;
+        }
+      }
+      s_tile = tk;
     }
-  } else {
-    Xsub[(int64_t)rows[R] * s + c] = acc;
+    __syncthreads();
+    const int tk = s_tile;
+    if (tk >= ntiles) break;
+    const int4 tile = tiles[tk];
+    sweep_tile<V, S, FWD, true>(tile, kk, ff, rowoff, Moff, M, rows, cptr, cidx, Doff, Dinv, Xsub, Wout, P, s,
+                                smem_raw);
+    __syncthreads();  // every write of the tile is issued
+    const int g = tile.x;
+    if (tid == 0) {
+      int fin = 1;  // the tile finished its row block
+      if (tile.w >= 0) {
+        __threadfence();
+        const int rb = slot_rb[tile.w];
+        fin = atomicAdd(rb_cnt + rb, 1) == rblocks[rb].z - 1 ? 2 : 0;  // 2: last partial, sum the row block
+        if (fin == 2) __threadfence();
+        s_flag = fin == 2 ? rb : -1;
+      } else {
+        s_flag = -1;
+      }
+      if (fin == 1) {
+        __threadfence();
+        if (atomicAdd(front_done + g, 1) == front_nrb[g] - 1 && FWD && parent[g] >= 0) {
+          __threadfence();
+          atomicAdd(child_ready + parent[g], 1);
+        }
+      }
+    }
+    __syncthreads();
+    const int rbl = s_flag;
+    if (rbl >= 0) {
+      const int4 rb = rblocks[rbl];
+      for (int e = tid; e < MF_TILE * s; e += MF_TILE)
+        rb_epilogue<V, FWD, true>(rb, e / s, e % s, kk, ff, rowoff, Doff, rows, cptr, cidx, Dinv, Wout, P, Xsub,
+                                  s);
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(front_done + g, 1) == front_nrb[g] - 1 && FWD && parent[g] >= 0) {
+          __threadfence();
+          atomicAdd(child_ready + parent[g], 1);
+        }
+      }
+    }
   }
 }
 
@@ -812,6 +964,36 @@ static void tc_launch(DevMF& mf, int l, V* Xsub, int s, cudaStream_t st) {
   }
 }
 
+// resident CTAs of k_mf_sweep<V, S, *> (set with the kernels' attributes, outside any capture)
+static int g_sweep_grid[2][7];
+template <typename V, int S>
+static int& sweep_grid() {
+  constexpr int vi = sizeof(V) == 8 ? 0 : 1;
+  constexpr int si = S == 1 ? 0 : S == 2 ? 1 : S == 4 ? 2 : S == 8 ? 3 : S == 16 ? 4 : S == 32 ? 5 : 6;
+  return g_sweep_grid[vi][si];
+}
+
+template <typename V, int S>
+static void sweep_persistent(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
+  const size_t shm = tile_smem_bytes<V, S>();
+  const int grid = sweep_grid<V, S>();
+  V* Wout = (V*)mf.Wout;
+  V* P = (V*)mf.P;
+  const V* Dv = (const V*)mf.Dinv;
+  cudaMemsetAsync(mf.cnt, 0, (size_t)mf.cnt_n * sizeof(int), st);
+  if (mf.pt_nf > 0)
+    { k_mf_sweep<V, S, true><<<std::min(grid, mf.pt_nf), MF_TILE, shm, st>>>(
+        mf.ptf, mf.pt_nf, mf.slot_rb_f, mf.prb_f, mf.nrb_f, mf.parent, mf.nchild, mf.cnt, mf.prb_nf,
+        (int)mf.nfronts, mf.sw_err, mf.k, mf.f, mf.rowoff, mf.Moff, (const V*)mf.M, mf.rows, mf.cptr, mf.cidx,
+        mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
+  cudaMemsetAsync(mf.cnt, 0, (size_t)mf.cnt_n * sizeof(int), st);
+  if (mf.pt_nb > 0)
+    { k_mf_sweep<V, S, false><<<std::min(grid, mf.pt_nb), MF_TILE, shm, st>>>(
+        mf.ptb, mf.pt_nb, mf.slot_rb_b, mf.prb_b, mf.nrb_b, mf.bdep, mf.nchild, mf.cnt, mf.prb_nb,
+        (int)mf.nfronts, mf.sw_err, mf.k, mf.f, mf.rowoff, mf.Moff, (const V*)mf.MT, mf.rows, mf.cptr, mf.cidx,
+        mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
+}
+
 template <typename V, int S>
 static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
   const size_t shm = tile_smem_bytes<V, S>();
@@ -824,6 +1006,10 @@ static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
   // tcgen05 kernel and the SIMT kernel (the tiles the SIMT kernel keeps are
   // the small ones); both write the same partial slots and epilogues
   const bool tc = tc_width<V, S>() && mf.tc;
+  if (!tc && mf.persistent && sweep_grid<V, S>() > 0) {
+    sweep_persistent<V, S>(mf, Xsub, s, st);
+    return;
+  }
   const int* fptr = tc ? mf.fs_ptr_h : mf.ftile_ptr_h;
   const int* bptr = tc ? mf.bs_ptr_h : mf.btile_ptr_h;
   const int4* ftl = tc ? mf.ftiles_s : mf.ftiles;
@@ -877,6 +1063,18 @@ static void tile_attrs() {
   const int shm = (int)tile_smem_bytes<V, S>();
   cudaFuncSetAttribute(k_mf_tile<V, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
   cudaFuncSetAttribute(k_mf_tile<V, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+  cudaFuncSetAttribute(k_mf_sweep<V, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+  cudaFuncSetAttribute(k_mf_sweep<V, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+  {
+    // resident CTAs per SM of the persistent sweep (the smaller of the two directions) x SMs
+    int dev = 0, sms = 0, a = 0, b = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mf_sweep<V, S, true>, MF_TILE, shm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_mf_sweep<V, S, false>, MF_TILE, shm);
+    sweep_grid<V, S>() = std::max(0, std::min(a, b)) * sms;
+    cudaGetLastError();
+  }
   if constexpr (tc_width<V, S>()) {
     const int tshm = (int)tc_smem_bytes<S>();
     cudaFuncSetAttribute(k_mf_tile_tc<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tshm);

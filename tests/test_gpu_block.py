@@ -39,7 +39,7 @@ def test_block_wavefields_match_oracle(cube, precision):
     u_or = oa.solve(A, F)
     its = {}
     for block in (0, 1):
-        with hz.Solver.from_problem(cube, rtol=1e-8, precision=precision, block_arnoldi=block) as S:
+        with hz.Solver.from_problem(cube, rtol=1e-8, precision=precision, block_arnoldi=block, max_block=16) as S:
             perm = dof_perm(S, space, 1000.0)
             u, st = S.solve(src)
             its[block] = st["iterations"]
@@ -51,7 +51,8 @@ def test_block_wavefields_match_oracle(cube, precision):
 
 def test_block_basis_is_orthonormal(cube):
     src = _sources(8, 4)
-    with hz.Solver.from_problem(cube, rtol=1e-10, block_arnoldi=1, coarse_mode=hz.HZ_COARSE_NONE, restart=12) as S:
+    with hz.Solver.from_problem(cube, rtol=1e-10, block_arnoldi=1, coarse_mode=hz.HZ_COARSE_NONE, restart=12,
+                                max_block=16) as S:
         S.solve(src)
         V = S.krylov_basis()
     nb, s, n = V.shape
@@ -68,7 +69,7 @@ def test_block_duplicated_sources(cube):
     src = np.array([[500.0, 500.0, 100.0]] * 3 + [[250.0, 700.0, 600.0]])
     space, A, F = oa.system(cube["fine"], cube["velocity"], cube["freq"], src)
     u_or = oa.solve(A, F)
-    with hz.Solver.from_problem(cube, rtol=1e-8, block_arnoldi=1) as S:
+    with hz.Solver.from_problem(cube, rtol=1e-8, block_arnoldi=1, max_block=16) as S:
         u, st = S.solve(src)
         res, its = S.column_stats()
         assert np.isfinite(u).all() and st["converged"] == 1
