@@ -86,7 +86,8 @@ typedef struct hz_options {
   int32_t coarse_mode;      /* HZ_COARSE_GMRES (default), HZ_COARSE_NONE, HZ_COARSE_DIRECT */
   int32_t coarse_inner_its; /* inner coarse GMRES iterations (10) */
   int32_t leaf_size;        /* nested-dissection leaf size (64) */
-  double pivot_tau;         /* static pivot perturbation, relative to max|A_i| (1e-12) */
+  double pivot_tau;         /* static pivot perturbation, relative to max|A_i| (1e-12; an FP32 factorisation
+                               uses at least 1e-6); 0 disables it (a zero pivot is then HZ_ESINGULAR) */
   int32_t verbose;          /* 0 silent */
   int32_t use_graphs;       /* 1 (default): replay the local-solve and coarse-solve launch sequences
                                as captured CUDA graphs; 0: launch them one by one */
@@ -112,6 +113,9 @@ typedef struct hz_options {
   int32_t persistent_sweeps;/* 1 (default): each SIMT front sweep is one launch over all tree levels (resident
                                CTAs take tiles in level order and wait for the fronts they depend on); 0: one
                                launch per level. The tensor-core tiles keep one launch per level */
+  int32_t factor_fp32;      /* mixed form only. 1 (default): the fine fronts are factorised (partial LDL^T and
+                               partitioned inverse) in complex FP32; 0: in FP64, then rounded to FP32. The
+                               coarse fronts are factorised in FP64 in both forms */
 } hz_options;
 
 typedef struct hz_stats {
@@ -144,6 +148,8 @@ typedef struct hz_info {
   double device_bytes;      /* device memory held by the context */
   int64_t kernel_launches;  /* kernels launched by the library in this process so far (kernels of
                                replayed CUDA graphs included) */
+  double factor_ldlt_seconds;    /* device time of the front assembly and partial LDL^T (both levels) */
+  double factor_inverse_seconds; /* device time of the partitioned inverses (both levels) */
 } hz_info;
 
 /* Fills *opt with the defaults listed above. */

@@ -85,6 +85,7 @@ struct DevPool {
 
 struct MFHost {
   int64_t factor_entries = 0, front_entries = 0, stored_entries = 0;
+  std::vector<int> fa_small_ptr, fa_big_ptr, fa_step_ptr, fa_tile_ptr;  // factorisation schedule
   int max_front = 0, nfronts = 0, nlevels = 0;
   std::vector<int> level_ptr, ftile_ptr, btile_ptr, frb_ptr, brb_ptr;
   std::vector<int> fs_ptr, bs_ptr, ftc_ptr, btc_ptr;  // tensor-core mode split of the tile lists
@@ -99,8 +100,8 @@ constexpr int MF_TILE_ROWS = 128;  // output rows per sweep tile (MF_TILE in mf.
 constexpr int MF_TILE_K = 128;     // reduction length per sweep tile (MF_TK in mf.cu)
 
 void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const FrontTree*>& trees,
-              const std::vector<int64_t>& sub_off, bool fp32, bool tc, bool persistent, DevMF& mf, MFHost& info,
-              DevPool& pool, cudaStream_t st) {
+              const std::vector<int64_t>& sub_off, bool fp32, bool fr32, bool tc, bool persistent, DevMF& mf,
+              MFHost& info, DevPool& pool, cudaStream_t st) {
   tc = tc && fp32;
   const size_t ns = mats.size();
   std::vector<int> base(ns + 1, 0);
@@ -274,11 +275,13 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
     for (int q = info.level_ptr[l]; q < info.level_ptr[l + 1]; ++q) {
       const int g = level_list[q];
       // a row block covered by a single tile finishes inside the tile (slot
-      // -1); the others sum their partial tiles in k_mf_reduce
+      // -1); the others sum their partial tiles in k_mf_reduce. A front
+      // without pivots (k = 0) still passes its children's updates on: its
+      // row blocks get one tile with an empty reduction
       for (int r0 = 0; r0 < f[g]; r0 += MF_TILE_ROWS) {
         const int kend = r0 < k[g] ? std::min(k[g], r0 + MF_TILE_ROWS) : k[g];
         const int nk = (kend + MF_TILE_K - 1) / MF_TILE_K;
-        if (nk == 1) {
+        if (nk <= 1) {
           ftiles.push_back(make_int4(g, r0, 0, -1));
           classify(true, ftiles.back());
           continue;
@@ -433,7 +436,53 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
   mf.amap_pos = pool.upload(amap_pos, st);
   mf.amap_val = pool.upload(amap_val, st);
   mf.Aval = pool.upload(Aval, st);
-  mf.F = pool.alloc<double2>(Foff[nf]);
+  mf.fr32 = fr32 ? 1 : 0;
+  mf.F = fr32 ? (void*)pool.alloc<float2>(Foff[nf]) : (void*)pool.alloc<double2>(Foff[nf]);
+  {
+    // factorisation schedule: small fronts one CTA each; large ones by panels with tiled trailing updates
+    std::vector<int> small, big;
+    std::vector<int4> ft;
+    info.fa_small_ptr.assign(1, 0);
+    info.fa_big_ptr.assign(1, 0);
+    info.fa_step_ptr.assign(1, 0);
+    info.fa_tile_ptr.assign(1, 0);
+    for (int l = 0; l <= maxh; ++l) {
+      int kmax = 0;
+      std::vector<int> lbig;
+      for (int q = info.level_ptr[l]; q < info.level_ptr[l + 1]; ++q) {
+        const int g = level_list[q];
+        if (f[g] <= FA_SMALL) {
+          small.push_back(g);
+        } else {
+          lbig.push_back(g);
+          kmax = std::max(kmax, k[g]);
+        }
+      }
+      big.insert(big.end(), lbig.begin(), lbig.end());
+      const int nsteps = lbig.empty() ? 0 : (kmax + FA_NB_H - 1) / FA_NB_H;
+      for (int p = 0; p < nsteps; ++p) {
+        const int p0 = p * FA_NB_H;
+        for (int g : lbig) {
+          if (p0 >= k[g]) continue;
+          const int q0 = p0 + std::min(FA_NB_H, k[g] - p0);
+          const int T = (f[g] - q0 + FA_TILE_H - 1) / FA_TILE_H;
+          for (int ti = 0; ti < T; ++ti)
+            for (int tj = 0; tj <= ti; ++tj) ft.push_back(make_int4(g, ti, tj, 0));
+        }
+        info.fa_tile_ptr.push_back((int)ft.size());
+      }
+      info.fa_small_ptr.push_back((int)small.size());
+      info.fa_big_ptr.push_back((int)big.size());
+      info.fa_step_ptr.push_back(info.fa_step_ptr.back() + nsteps);
+    }
+    mf.fa_small = pool.upload(small, st);
+    mf.fa_big = pool.upload(big, st);
+    mf.fa_tiles = pool.upload(ft, st);
+    mf.fa_small_ptr_h = info.fa_small_ptr.data();
+    mf.fa_big_ptr_h = info.fa_big_ptr.data();
+    mf.fa_step_ptr_h = info.fa_step_ptr.data();
+    mf.fa_tile_ptr_h = info.fa_tile_ptr.data();
+  }
   mf.perturbed = pool.alloc<int>(1);
   CK(cudaMemsetAsync(mf.perturbed, 0, sizeof(int), st));
   mf.tc = tc ? 1 : 0;
@@ -518,8 +567,8 @@ struct LevelDev {             // one level of ORAS on the device
   double amax = 0.0;
 };
 
-void build_level(const Space& sp, const std::vector<Subdomain>& subs, int leaf, bool fp32, bool tc, bool persistent,
-                 LevelDev& L, DevPool& pool, cudaStream_t st) {
+void build_level(const Space& sp, const std::vector<Subdomain>& subs, int leaf, bool fp32, bool fr32, bool tc,
+                 bool persistent, LevelDev& L, DevPool& pool, cudaStream_t st) {
   const size_t np = subs.size();
   std::vector<int64_t> sub_off(np + 1, 0);
   for (size_t i = 0; i < np; ++i) sub_off[i + 1] = sub_off[i] + (int64_t)subs[i].dofs.size();
@@ -541,7 +590,7 @@ void build_level(const Space& sp, const std::vector<Subdomain>& subs, int leaf, 
     tr[i] = &L.trees[i];
     for (const cplx& v : subs[i].A.val) L.amax = std::max(L.amax, std::abs(v));
   }
-  build_mf(mats, tr, sub_off, fp32, tc, persistent, L.mf, L.info, pool, st);
+  build_mf(mats, tr, sub_off, fp32, fr32, tc, persistent, L.mf, L.info, pool, st);
   std::vector<int> gidx(sub_off[np]), own(sp.n, -1);
   for (size_t i = 0; i < np; ++i)
     for (size_t l = 0; l < subs[i].dofs.size(); ++l) {
@@ -557,13 +606,13 @@ void build_level(const Space& sp, const std::vector<Subdomain>& subs, int leaf, 
 
 // A single "subdomain" covering the whole matrix: direct factorisation.
 void build_direct(const Space& sp, const CsrC& A, int leaf, bool fp32, bool tc, bool persistent, LevelDev& L,
-                  DevPool& pool, cudaStream_t st) {
+                  DevPool& pool, cudaStream_t st) {  // the coarse factors: factorised in FP64
   std::vector<Subdomain> one(1);
   one[0].dofs.resize(sp.n);
   std::iota(one[0].dofs.begin(), one[0].dofs.end(), 0);
   one[0].owned.assign(sp.n, 1);
   one[0].A = A;
-  build_level(sp, one, leaf, fp32, tc, persistent, L, pool, st);
+  build_level(sp, one, leaf, fp32, false, tc, persistent, L, pool, st);
 }
 
 void mesh_from_abi(const hz_mesh* in, Mesh& m) {
@@ -1254,6 +1303,7 @@ int hz_default_options(hz_options* o) {
   o->debug_bounds = 0;
   o->block_arnoldi = 0;
   o->persistent_sweeps = 1;
+  o->factor_fp32 = 1;
   return HZ_OK;
 }
 
@@ -1313,7 +1363,7 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
     std::vector<Subdomain> subs = build_subdomains(c->fine, c->space, part, nparts, mvals, omega, o.overlap);
     const bool tc = mixed && o.tensor_cores != 0;
     const bool pers = o.persistent_sweeps != 0;
-    build_level(c->space, subs, o.leaf_size, mixed, tc, pers, c->lf, c->pool, c->st);
+    build_level(c->space, subs, o.leaf_size, mixed, mixed && o.factor_fp32 != 0, tc, pers, c->lf, c->pool, c->st);
     subs.clear();
     if (o.coarse_mode != HZ_COARSE_NONE) {
       c->has_coarse = true;
@@ -1331,14 +1381,16 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
       if (o.coarse_mode == HZ_COARSE_GMRES) {
         std::vector<Subdomain> csubs =
             build_subdomains(c->coarse, c->cspace, C.part, nparts, C.mvals, omega, o.overlap);
-        build_level(c->cspace, csubs, o.leaf_size, mixed, tc, pers, c->lc, c->pool, c->st);
+        build_level(c->cspace, csubs, o.leaf_size, mixed, false, tc, pers, c->lc, c->pool, c->st);
       } else {
         build_direct(c->cspace, C.E, o.leaf_size, mixed, tc, pers, c->lc, c->pool, c->st);
       }
     }
     CK(cudaStreamSynchronize(c->st));
     const double t1 = now_s();
-    mf_factor(c->lf.mf, o.pivot_tau * c->lf.amax, c->st);
+    // an FP32 factorisation perturbs pivots below 1e-6 of max|A_i| (FP32 round-off scale), FP64 below pivot_tau
+    const double tau_f = (c->lf.mf.fr32 && o.pivot_tau > 0.0) ? std::max(o.pivot_tau, 1e-6) : o.pivot_tau;
+    mf_factor(c->lf.mf, tau_f * c->lf.amax, c->st);
     check_launch();
     if (c->has_coarse) {
       mf_factor(c->lc.mf, o.pivot_tau * c->lc.amax, c->st);
@@ -1350,10 +1402,10 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
     CK(cudaStreamSynchronize(c->st));
     c->factor_s = now_s() - t1;
     // the f x f workspaces are only needed by the factorisation
-    c->pool.free_one(c->lf.mf.F, c->lf.mf.F_total * sizeof(double2));
+    c->pool.free_one(c->lf.mf.F, c->lf.mf.F_total * (c->lf.mf.fr32 ? sizeof(float2) : sizeof(double2)));
     c->lf.mf.F = nullptr;
     if (c->has_coarse) {
-      c->pool.free_one(c->lc.mf.F, c->lc.mf.F_total * sizeof(double2));
+      c->pool.free_one(c->lc.mf.F, c->lc.mf.F_total * (c->lc.mf.fr32 ? sizeof(float2) : sizeof(double2)));
       c->lc.mf.F = nullptr;
     }
     c->perturbed = pf + pcnt;
@@ -1415,6 +1467,8 @@ int hz_get_info(const hz_ctx* c, hz_info* info) {
   info->perturbed_pivots = c->perturbed;
   info->device_bytes = c->pool.bytes + c->work.bytes;
   info->kernel_launches = g_kernel_launches.load();
+  info->factor_ldlt_seconds = 1e-3 * (c->lf.mf.factor_ms + c->lc.mf.factor_ms);
+  info->factor_inverse_seconds = 1e-3 * (c->lf.mf.inverse_ms + c->lc.mf.inverse_ms);
   return HZ_OK;
 }
 

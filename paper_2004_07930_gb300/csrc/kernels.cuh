@@ -68,7 +68,18 @@ struct DevMF {
   int* amap_pos = nullptr;      // front position r + c f of each assembled entry
   int64_t* amap_val = nullptr;  // index into Aval
   double2* Aval = nullptr;      // concatenated local matrix values
-  double2* F = nullptr;         // factorisation workspace (freed after setup)
+  void* F = nullptr;            // factorisation workspace, double2 or float2 (fr32), freed after setup
+  int fr32 = 0;                 // factorisation in complex FP32 (mixed form, fine level)
+  float factor_ms = 0.f, inverse_ms = 0.f;  // device time of the assembly + LDL^T and of the partitioned inverse
+  // factorisation schedule: per level the fronts factored pivot by pivot (f <= FA_SMALL) and the
+  // fronts factored by panels; per panel step the trailing-update tiles (front, tile row, tile column)
+  int* fa_small = nullptr;
+  int* fa_small_ptr_h = nullptr;  // host [nlevels+1]
+  int* fa_big = nullptr;
+  int* fa_big_ptr_h = nullptr;    // host [nlevels+1]
+  int* fa_step_ptr_h = nullptr;   // host [nlevels+1] panel steps of each level (prefix)
+  int4* fa_tiles = nullptr;
+  int* fa_tile_ptr_h = nullptr;   // host [steps+1]
   void* M = nullptr;            // X_t factors (double2 or float2), column-major f x k
   void* MT = nullptr;           // X_t^T, column-major k x f (backward sweep)
   void* Dinv = nullptr;         // 1/D (double2 or float2)
@@ -120,6 +131,12 @@ struct DevMF {
   int* sw_err = nullptr;        // device flag: a persistent sweep gave up waiting
   int sweep_grid = 0;           // resident CTAs of the sweep kernel
 };
+
+// fronts of order <= FA_SMALL are factored pivot by pivot, larger ones by panels of FA_NB_H pivots
+// with FA_TILE_H x FA_TILE_H trailing-update tiles (FA_NB / FA_TILE in factor.cu)
+constexpr int FA_SMALL = 160;
+constexpr int FA_NB_H = 32;
+constexpr int FA_TILE_H = 64;
 
 // tensor-core tile eligibility (output rows, reduction length) and packing geometry
 constexpr int TC_MIN_ROWS = 32;

@@ -1,12 +1,5 @@
-// Batched multifrontal factorisation and partitioned-inverse solves of the
-// local matrices A_i (the paper's direct local solver inside Eq. oras).
-//
-// Factorisation: every front F_t (order f = k + m, k pivots) is assembled
-// from the entries of A_i and its children's Schur complements (extend-add),
-// then partially factored as F_t = L D L^T on its k pivots (complex
-// symmetric, no pivoting, static perturbation of tiny pivots); the trailing
-// m x m block becomes the Schur complement passed to the parent. All fronts
-// of one tree height, over all subdomains, are processed by one launch.
+// Partitioned-inverse solves of the local matrices A_i (the paper's direct
+// local solver inside Eq. oras); the factorisation is in factor.cu.
 //
 // Partitioned inverse: the first k columns of the inverse of the unit lower
 // trapezoid [[L11, 0], [L21, I]] are stored, X_t = [L11^{-1}; -L21 L11^{-1}]
@@ -75,160 +68,19 @@ __device__ __forceinline__ double2 zcdiv(double2 a, double2 b) {
   return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
 
-// ---------------------------------------------------------------------------
-// Assembly (extend-add), partial LDL^T, partitioned inverse
-// ---------------------------------------------------------------------------
-__global__ void k_mf_assemble(const int* __restrict__ list, const int* __restrict__ kk, const int* __restrict__ ff,
-                              const int64_t* __restrict__ Foff, const int64_t* __restrict__ rowoff,
-                              const int* __restrict__ cmap, const int* __restrict__ child_ptr,
-                              const int* __restrict__ child_idx, const int64_t* __restrict__ amap_ptr,
-                              const int* __restrict__ amap_pos, const int64_t* __restrict__ amap_val,
-                              const double2* __restrict__ Aval, double2* __restrict__ F) {
-  const int t = list[blockIdx.x];
-  const int f = ff[t];
-  double2* Ft = F + Foff[t];
-  const int64_t ff2 = (int64_t)f * f;
-  for (int64_t i = threadIdx.x; i < ff2; i += blockDim.x) Ft[i] = make_double2(0.0, 0.0);
-  __syncthreads();
-  for (int64_t p = amap_ptr[t] + threadIdx.x; p < amap_ptr[t + 1]; p += blockDim.x) {
-    double2 a = Aval[amap_val[p]];
-    double2 v = Ft[amap_pos[p]];
-    Ft[amap_pos[p]] = make_double2(v.x + a.x, v.y + a.y);
-  }
-  __syncthreads();
-  for (int q = child_ptr[t]; q < child_ptr[t + 1]; ++q) {
-    const int ch = child_idx[q];
-    const int kc = kk[ch], fc = ff[ch], mc = fc - kc;
-    const double2* Fc = F + Foff[ch];
-    const int* cm = cmap + rowoff[ch] + kc;
-    const int64_t mm = (int64_t)mc * mc;
-    for (int64_t i = threadIdx.x; i < mm; i += blockDim.x) {
-      int a = (int)(i % mc), b = (int)(i / mc);
-      if (a < b) continue;
-      int64_t dst = cm[a] + (int64_t)cm[b] * f;
-      double2 s = Fc[(kc + a) + (int64_t)(kc + b) * fc];
-      double2 v = Ft[dst];
-      Ft[dst] = make_double2(v.x + s.x, v.y + s.y);
-    }
-    __syncthreads();
-  }
-}
-
-__global__ void k_mf_factor(const int* __restrict__ list, const int* __restrict__ kk, const int* __restrict__ ff,
-                            const int64_t* __restrict__ Foff, double2* __restrict__ F, double tau_abs,
-                            int* perturbed) {
-  extern __shared__ double2 col[];
-  __shared__ double2 dinv_s;
-  const int t = list[blockIdx.x];
-  const int f = ff[t], k = kk[t];
-  double2* Ft = F + Foff[t];
-  for (int j = 0; j < k; ++j) {
-    if (threadIdx.x == 0) {
-      double2 d = Ft[j + (int64_t)j * f];
-      double ad = sqrt(d.x * d.x + d.y * d.y);
-      if (ad < tau_abs) {
-        d = ad > 0.0 ? make_double2(d.x / ad * tau_abs, d.y / ad * tau_abs) : make_double2(tau_abs, 0.0);
-        Ft[j + (int64_t)j * f] = d;
-        atomicAdd(perturbed, 1);
-      }
-      dinv_s = zcdiv(make_double2(1.0, 0.0), d);
-    }
-    for (int r = j + 1 + threadIdx.x; r < f; r += blockDim.x) col[r] = Ft[r + (int64_t)j * f];
-    __syncthreads();
-    const double2 dinv = dinv_s;
-    for (int r = j + 1 + threadIdx.x; r < f; r += blockDim.x) Ft[r + (int64_t)j * f] = c_mul(col[r], dinv);
-    const int nn = f - j - 1;
-    const int64_t nn2 = (int64_t)nn * nn;
-    for (int64_t i = threadIdx.x; i < nn2; i += blockDim.x) {
-      int r = j + 1 + (int)(i % nn), c = j + 1 + (int)(i / nn);
-      if (r < c) continue;
-      int64_t o = r + (int64_t)c * f;
-      double2 u = c_mul(col[r], c_mul(col[c], dinv));
-      double2 v = Ft[o];
-      Ft[o] = make_double2(v.x - u.x, v.y - u.y);
-    }
-    __syncthreads();
-  }
-}
-
-// In place on the first k columns: L -> X = first k columns of
-// [[L11,0],[L21,I]]^{-1}; stores 1/D and copies X into the compact factor
-// array (FP64 or FP32).
-template <typename V>
-__global__ void k_mf_inverse(const int* __restrict__ list, const int* __restrict__ kk, const int* __restrict__ ff,
-                             const int64_t* __restrict__ Foff, const int64_t* __restrict__ Moff,
-                             const int64_t* __restrict__ Doff, double2* __restrict__ F, V* __restrict__ M,
-                             V* __restrict__ MT, V* __restrict__ Dinv) {
-  extern __shared__ double2 col[];
-  const int t = list[blockIdx.x];
-  const int f = ff[t], k = kk[t];
-  double2* Ft = F + Foff[t];
-  for (int j = threadIdx.x; j < k; j += blockDim.x)
-    Dinv[Doff[t] + j] = from_d<V>(zcdiv(make_double2(1.0, 0.0), Ft[j + (int64_t)j * f]));
-  __syncthreads();
-  for (int l = 0; l < k; ++l) {
-    for (int r = l + 1 + threadIdx.x; r < f; r += blockDim.x) col[r] = Ft[r + (int64_t)l * f];
-    __syncthreads();
-    // X[r][c] -= L[r][l] X[l][c] for c < l, r > l;  X[r][l] = -L[r][l]
-    const int nr = f - l - 1;
-    const int64_t work = (int64_t)nr * (l + 1);
-    for (int64_t i = threadIdx.x; i < work; i += blockDim.x) {
-      int r = l + 1 + (int)(i % nr), c = (int)(i / nr);
-      int64_t o = r + (int64_t)c * f;
-      if (c == l) {
-        Ft[o] = make_double2(-col[r].x, -col[r].y);
-      } else {
-        double2 x = Ft[l + (int64_t)c * f];
-        double2 u = c_mul(col[r], x);
-        double2 v = Ft[o];
-        Ft[o] = make_double2(v.x - u.x, v.y - u.y);
-      }
-    }
-    __syncthreads();
-  }
-  V* Mt = M + Moff[t];
-  V* MTt = MT + Moff[t];
-  const int64_t fk = (int64_t)f * k;
-  for (int64_t i = threadIdx.x; i < fk; i += blockDim.x) {
-    int r = (int)(i % f), c = (int)(i / f);
-    double2 v = r == c ? make_double2(1.0, 0.0) : (r < c ? make_double2(0.0, 0.0) : Ft[i]);
-    Mt[i] = from_d<V>(v);
-    MTt[c + (int64_t)r * k] = from_d<V>(v);
-  }
-}
-
 template <typename V>
 static void tile_attrs_all();
 static void tc_pack_all(DevMF& mf, cudaStream_t st);
+void mf_factor_fronts(DevMF& mf, double tau_abs, cudaStream_t st);  // factor.cu
 
+// Numeric factorisation and partitioned inverse (factor.cu), then the
+// sweep kernels' attributes and the tensor-core tile packing.
 void mf_factor(DevMF& mf, double tau_abs, cudaStream_t st) {
   if (mf.fp32)
     tile_attrs_all<float2>();
   else
     tile_attrs_all<double2>();
-  size_t shm = (size_t)std::max(mf.max_f, 1) * sizeof(double2);
-  cudaFuncSetAttribute(k_mf_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-  cudaFuncSetAttribute(k_mf_inverse<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-  cudaFuncSetAttribute(k_mf_inverse<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-  for (int l = 0; l < mf.nlevels; ++l) {
-    int b = mf.level_ptr_h[l], e = mf.level_ptr_h[l + 1];
-    if (e == b) continue;
-    { k_mf_assemble<<<e - b, 256, 0, st>>>(mf.level_list + b, mf.k, mf.f, mf.Foff, mf.rowoff, mf.cmap, mf.child_ptr,
-                                         mf.child_idx, mf.amap_ptr, mf.amap_pos, mf.amap_val, mf.Aval, mf.F); count_launch(); }
-    { k_mf_factor<<<e - b, 256, shm, st>>>(mf.level_list + b, mf.k, mf.f, mf.Foff, mf.F, tau_abs, mf.perturbed); count_launch(); }
-  }
-  // the inverses only touch the pivot columns: run them after every Schur
-  // complement has been consumed by its parent
-  for (int l = 0; l < mf.nlevels; ++l) {
-    int b = mf.level_ptr_h[l], e = mf.level_ptr_h[l + 1];
-    if (e == b) continue;
-    if (mf.fp32)
-      { k_mf_inverse<float2><<<e - b, 256, shm, st>>>(mf.level_list + b, mf.k, mf.f, mf.Foff, mf.Moff, mf.Doff, mf.F,
-                                                    (float2*)mf.M, (float2*)mf.MT, (float2*)mf.Dinv); count_launch(); }
-    else
-      { k_mf_inverse<double2><<<e - b, 256, shm, st>>>(mf.level_list + b, mf.k, mf.f, mf.Foff, mf.Moff, mf.Doff,
-                                                     mf.F, (double2*)mf.M, (double2*)mf.MT, (double2*)mf.Dinv); count_launch(); }
-  }
+  mf_factor_fronts(mf, tau_abs, st);
   // tensor-core tiles: pack their factor blocks from X_t (forward) and X_t^T (backward)
   if (mf.tc && mf.fp32) tc_pack_all(mf, st);
 }

@@ -37,7 +37,7 @@ class HzOptions(C.Structure):
                 ("leaf_size", C.c_int32), ("pivot_tau", C.c_double), ("verbose", C.c_int32),
                 ("use_graphs", C.c_int32), ("tensor_cores", C.c_int32), ("overlap", C.c_int32),
                 ("coarse_fp32", C.c_int32), ("debug_bounds", C.c_int32), ("block_arnoldi", C.c_int32),
-                ("persistent_sweeps", C.c_int32)]
+                ("persistent_sweeps", C.c_int32), ("factor_fp32", C.c_int32)]
 
 
 class HzStats(C.Structure):
@@ -55,7 +55,8 @@ class HzInfo(C.Structure):
                 ("factor_entries", C.c_int64), ("coarse_factor_entries", C.c_int64),
                 ("front_entries", C.c_int64), ("max_front", C.c_int32), ("nfronts", C.c_int32),
                 ("nlevels", C.c_int32), ("perturbed_pivots", C.c_int32), ("device_bytes", C.c_double),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("factor_ldlt_seconds", C.c_double),
+                ("factor_inverse_seconds", C.c_double)]
 
     def asdict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
