@@ -350,6 +350,159 @@ __global__ void k_fa_inverse(const int* __restrict__ list, const int* __restrict
 }
 
 // ---------------------------------------------------------------------------
+// Large fronts: blocked partitioned inverse, in place. X = L~^{-1} E_k with
+// L~ = [[L11, 0], [L21, I]] and E_k the first k columns of the identity,
+// by row blocks B = [l0, l0 + nb) of the pivot region:
+//   X[B, :] <- L~[B, B]^{-1} X[B, :]                  (k_fa_inv_diag)
+//   X[r, :] <- X[r, :] - L~[r, B] X[B, :], r > B      (k_fa_inv_update)
+// where X starts as E_k. X[r][c] (c < k) shares its storage with L[r][c]:
+// the first step copies the panel L[r, B] of the rows below B to a scratch
+// panel before the update overwrites it, and the identity entries (the
+// diagonal, which keeps d, and the upper triangle) are never stored.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(FA_THREADS) k_fa_inv_diag(const int* __restrict__ list, const int* __restrict__ kk,
+                                                            const int* __restrict__ ff,
+                                                            const int64_t* __restrict__ Foff, T* __restrict__ F,
+                                                            const int64_t* __restrict__ pan_off, T* __restrict__ pan,
+                                                            int l0) {
+  __shared__ T Lb[FA_NB][FA_NB + 1];
+  const int t = list[blockIdx.x];
+  const int f = ff[t], k = kk[t];
+  if (l0 >= k) return;
+  const int nb = min(FA_NB, k - l0);
+  T* Ft = F + Foff[t];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < nb * nb; e += FA_THREADS) {
+    const int r = e % nb, c = e / nb;
+    if (r > c) Lb[r][c] = Ft[(l0 + r) + (int64_t)(l0 + c) * f];
+  }
+  // scratch panel: L[r][l0 + j] of the rows below the block, [r - l0 - nb][j]
+  T* P = pan + pan_off[blockIdx.x];
+  const int below = f - l0 - nb;
+  for (int64_t e = tid; e < (int64_t)below * nb; e += FA_THREADS) {
+    const int i = (int)(e % below), j = (int)(e / below);
+    P[(int64_t)i * FA_NB + j] = Ft[(l0 + nb + i) + (int64_t)(l0 + j) * f];
+  }
+  __syncthreads();
+  // X[B, c] for c < l0 + nb: forward substitution with the unit lower block, one thread per column
+  for (int c = tid; c < l0 + nb; c += FA_THREADS) {
+    T x[FA_NB];
+#pragma unroll
+    for (int l = 0; l < FA_NB; ++l) {
+      if (l >= nb) break;
+      const int gl = l0 + l;
+      T v = c < l0 ? Ft[gl + (int64_t)c * f] : (gl == c ? mkc((typename Cx<T>::R)1, (typename Cx<T>::R)0, T())
+                                                          : czero<T>());
+#pragma unroll
+      for (int q = 0; q < FA_NB; ++q) {
+        if (q >= l) break;
+        v = cfms(Lb[l][q], x[q], v);
+      }
+      x[l] = v;
+    }
+#pragma unroll
+    for (int l = 0; l < FA_NB; ++l) {
+      if (l >= nb) break;
+      if (l0 + l > c) Ft[(l0 + l) + (int64_t)c * f] = x[l];
+    }
+  }
+}
+
+// X[r][c] = base - sum_{l in B} L[r][l] X[l][c] on the 64 x 64 tile (ti, tj)
+// of rows [l0 + nb, f) x columns [0, l0 + nb); base = X[r][c] for c < l0, 0
+// for c in B. X[l][c] for l in B: the stored entry below the diagonal, 1 on
+// it, 0 above.
+template <typename T>
+__global__ void __launch_bounds__(FA_THREADS) k_fa_inv_update(const int4* __restrict__ tiles,
+                                                              const int* __restrict__ kk, const int* __restrict__ ff,
+                                                              const int64_t* __restrict__ Foff, T* __restrict__ F,
+                                                              const int64_t* __restrict__ pan_off,
+                                                              const T* __restrict__ pan, int l0) {
+  extern __shared__ __align__(16) unsigned char fa_smem[];
+  T(*As)[FA_TILE] = reinterpret_cast<T(*)[FA_TILE]>(fa_smem);                                // [NB][64] L[r][l]
+  T(*Bs)[FA_TILE] = reinterpret_cast<T(*)[FA_TILE]>(fa_smem + sizeof(T) * FA_NB * FA_TILE);  // [NB][64] X[l][c]
+  const int4 tl = tiles[blockIdx.x];
+  const int t = tl.x;
+  const int f = ff[t], k = kk[t];
+  const int nb = min(FA_NB, k - l0);
+  const int q0 = l0 + nb;
+  const int r0 = q0 + tl.y * FA_TILE, c0 = tl.z * FA_TILE;
+  T* Ft = F + Foff[t];
+  const T* P = pan + pan_off[tl.w];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < FA_NB * FA_TILE; e += FA_THREADS) {
+    const int i = e % FA_TILE, j = e / FA_TILE;
+    T a = czero<T>(), b = czero<T>();
+    if (j < nb) {
+      if (r0 + i < f) a = P[(int64_t)(r0 + i - q0) * FA_NB + j];
+      const int c = c0 + i, l = l0 + j;
+      if (c < q0)
+        b = l > c ? Ft[l + (int64_t)c * f]
+                  : (l == c ? mkc((typename Cx<T>::R)1, (typename Cx<T>::R)0, T()) : czero<T>());
+    }
+    As[j][i] = a;
+    Bs[j][i] = b;
+  }
+  __syncthreads();
+  const int tx = tid % 16, ty = tid / 16;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = czero<T>();
+  for (int j = 0; j < nb; ++j) {
+    T av[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) av[a] = As[j][ty * 4 + a];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) bv[b] = Bs[j][tx * 4 + b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        acc[a][b].x = fma(av[a].x, bv[b].x, fma(-av[a].y, bv[b].y, acc[a][b].x));
+        acc[a][b].y = fma(av[a].x, bv[b].y, fma(av[a].y, bv[b].x, acc[a][b].y));
+      }
+  }
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int c = c0 + tx * 4 + b;
+    if (c >= q0) continue;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int r = r0 + ty * 4 + a;
+      if (r >= f) continue;
+      const int64_t o = r + (int64_t)c * f;
+      const T base = c < l0 ? Ft[o] : czero<T>();
+      Ft[o] = csub(base, acc[a][b]);
+    }
+  }
+}
+
+// 1/D and X_t (and X_t^T) to the factor arrays, after the blocked inverse
+template <typename T, typename V>
+__global__ void k_fa_store(const int* __restrict__ list, const int* __restrict__ kk, const int* __restrict__ ff,
+                           const int64_t* __restrict__ Foff, const int64_t* __restrict__ Moff,
+                           const int64_t* __restrict__ Doff, const T* __restrict__ F, V* __restrict__ M,
+                           V* __restrict__ MT, V* __restrict__ Dinv) {
+  const int t = list[blockIdx.x];
+  const int f = ff[t], k = kk[t];
+  const T* Ft = F + Foff[t];
+  for (int j = threadIdx.x; j < k; j += blockDim.x)
+    Dinv[Doff[t] + j] = from_d2<V>(to_d(cinv(Ft[j + (int64_t)j * f])));
+  V* Mt = M + Moff[t];
+  V* MTt = MT + Moff[t];
+  const int64_t fk = (int64_t)f * k;
+  for (int64_t i = threadIdx.x; i < fk; i += blockDim.x) {
+    const int r = (int)(i % f), c = (int)(i / f);
+    const double2 v = r == c ? make_double2(1.0, 0.0) : (r < c ? make_double2(0.0, 0.0) : to_d(Ft[i]));
+    Mt[i] = from_d2<V>(v);
+    MTt[c + (int64_t)r * k] = from_d2<V>(v);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 template <typename T, typename V>
@@ -386,12 +539,28 @@ static void factor_t(DevMF& mf, double tau_abs, cudaStream_t st) {
   }
   cudaEventRecord(ev[1], st);
   // the inverses only touch the pivot columns: run them after every Schur
-  // complement has been consumed by its parent
+  // complement has been consumed by its parent; small fronts one CTA each,
+  // large fronts by row blocks (the same steps as their panels)
+  cudaFuncSetAttribute(k_fa_inv_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)schur_shm);
+  T* pan = reinterpret_cast<T*>(mf.fa_pan);
   for (int l = 0; l < mf.nlevels; ++l) {
-    const int b = mf.level_ptr_h[l], e = mf.level_ptr_h[l + 1];
-    if (e == b) continue;
-    { k_fa_inverse<T, V><<<e - b, 256, shm, st>>>(mf.level_list + b, mf.k, mf.f, mf.Foff, mf.Moff, mf.Doff, F,
-                                                  (V*)mf.M, (V*)mf.MT, (V*)mf.Dinv); count_launch(); }
+    const int sb = mf.fa_small_ptr_h[l], se = mf.fa_small_ptr_h[l + 1];
+    if (se > sb)
+      { k_fa_inverse<T, V><<<se - sb, 256, shm, st>>>(mf.fa_small + sb, mf.k, mf.f, mf.Foff, mf.Moff, mf.Doff, F,
+                                                      (V*)mf.M, (V*)mf.MT, (V*)mf.Dinv); count_launch(); }
+    const int bb = mf.fa_big_ptr_h[l], be = mf.fa_big_ptr_h[l + 1];
+    if (be == bb) continue;
+    for (int p = mf.fa_step_ptr_h[l]; p < mf.fa_step_ptr_h[l + 1]; ++p) {
+      const int l0 = (p - mf.fa_step_ptr_h[l]) * FA_NB;
+      { k_fa_inv_diag<T><<<be - bb, FA_THREADS, 0, st>>>(mf.fa_big + bb, mf.k, mf.f, mf.Foff, F, mf.fa_pan_off + bb,
+                                                         pan, l0); count_launch(); }
+      const int tb = mf.fi_tile_ptr_h[p], te = mf.fi_tile_ptr_h[p + 1];
+      if (te > tb)
+        { k_fa_inv_update<T><<<te - tb, FA_THREADS, schur_shm, st>>>(mf.fi_tiles + tb, mf.k, mf.f, mf.Foff, F,
+                                                                     mf.fa_pan_off + bb, pan, l0); count_launch(); }
+    }
+    { k_fa_store<T, V><<<be - bb, 256, 0, st>>>(mf.fa_big + bb, mf.k, mf.f, mf.Foff, mf.Moff, mf.Doff, F, (V*)mf.M,
+                                                (V*)mf.MT, (V*)mf.Dinv); count_launch(); }
   }
   cudaEventRecord(ev[2], st);
   cudaEventSynchronize(ev[2]);

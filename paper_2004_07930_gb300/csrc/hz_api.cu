@@ -85,7 +85,7 @@ struct DevPool {
 
 struct MFHost {
   int64_t factor_entries = 0, front_entries = 0, stored_entries = 0;
-  std::vector<int> fa_small_ptr, fa_big_ptr, fa_step_ptr, fa_tile_ptr;  // factorisation schedule
+  std::vector<int> fa_small_ptr, fa_big_ptr, fa_step_ptr, fa_tile_ptr, fi_tile_ptr;  // factorisation schedule
   int max_front = 0, nfronts = 0, nlevels = 0;
   std::vector<int> level_ptr, ftile_ptr, btile_ptr, frb_ptr, brb_ptr;
   std::vector<int> fs_ptr, bs_ptr, ftc_ptr, btc_ptr;  // tensor-core mode split of the tile lists
@@ -441,11 +441,14 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
   {
     // factorisation schedule: small fronts one CTA each; large ones by panels with tiled trailing updates
     std::vector<int> small, big;
-    std::vector<int4> ft;
+    std::vector<int4> ft, fi;
+    std::vector<int64_t> pan_off;
+    int64_t pan_total = 0;
     info.fa_small_ptr.assign(1, 0);
     info.fa_big_ptr.assign(1, 0);
     info.fa_step_ptr.assign(1, 0);
     info.fa_tile_ptr.assign(1, 0);
+    info.fi_tile_ptr.assign(1, 0);
     for (int l = 0; l <= maxh; ++l) {
       int kmax = 0;
       std::vector<int> lbig;
@@ -458,19 +461,31 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
           kmax = std::max(kmax, k[g]);
         }
       }
+      const int bfirst = (int)big.size();
       big.insert(big.end(), lbig.begin(), lbig.end());
+      for (int g : lbig) {
+        pan_off.push_back(pan_total);
+        pan_total += (int64_t)f[g] * FA_NB_H;
+      }
       const int nsteps = lbig.empty() ? 0 : (kmax + FA_NB_H - 1) / FA_NB_H;
       for (int p = 0; p < nsteps; ++p) {
         const int p0 = p * FA_NB_H;
-        for (int g : lbig) {
+        for (size_t bi = 0; bi < lbig.size(); ++bi) {
+          const int g = lbig[bi];
           if (p0 >= k[g]) continue;
           const int q0 = p0 + std::min(FA_NB_H, k[g] - p0);
           const int T = (f[g] - q0 + FA_TILE_H - 1) / FA_TILE_H;
           for (int ti = 0; ti < T; ++ti)
             for (int tj = 0; tj <= ti; ++tj) ft.push_back(make_int4(g, ti, tj, 0));
+          // inverse: rows below the block x columns [0, q0); w = the front's index in the level's big list
+          const int Tc = (q0 + FA_TILE_H - 1) / FA_TILE_H;
+          for (int ti = 0; ti < T; ++ti)
+            for (int tj = 0; tj < Tc; ++tj) fi.push_back(make_int4(g, ti, tj, (int)bi));
         }
         info.fa_tile_ptr.push_back((int)ft.size());
+        info.fi_tile_ptr.push_back((int)fi.size());
       }
+      (void)bfirst;
       info.fa_small_ptr.push_back((int)small.size());
       info.fa_big_ptr.push_back((int)big.size());
       info.fa_step_ptr.push_back(info.fa_step_ptr.back() + nsteps);
@@ -478,6 +493,11 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
     mf.fa_small = pool.upload(small, st);
     mf.fa_big = pool.upload(big, st);
     mf.fa_tiles = pool.upload(ft, st);
+    mf.fi_tiles = pool.upload(fi, st);
+    mf.fa_pan_off = pool.upload(pan_off, st);
+    mf.fa_pan = fr32 ? (void*)pool.alloc<float2>(std::max<int64_t>(pan_total, 1))
+                     : (void*)pool.alloc<double2>(std::max<int64_t>(pan_total, 1));
+    mf.fi_tile_ptr_h = info.fi_tile_ptr.data();
     mf.fa_small_ptr_h = info.fa_small_ptr.data();
     mf.fa_big_ptr_h = info.fa_big_ptr.data();
     mf.fa_step_ptr_h = info.fa_step_ptr.data();

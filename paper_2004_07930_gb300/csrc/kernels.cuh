@@ -80,6 +80,10 @@ struct DevMF {
   int* fa_step_ptr_h = nullptr;   // host [nlevels+1] panel steps of each level (prefix)
   int4* fa_tiles = nullptr;
   int* fa_tile_ptr_h = nullptr;   // host [steps+1]
+  int4* fi_tiles = nullptr;       // blocked inverse: update tiles (front, tile row, tile column, panel slot)
+  int* fi_tile_ptr_h = nullptr;   // host [steps+1]
+  int64_t* fa_pan_off = nullptr;  // [big fronts] offset of each large front's scratch panel (f x FA_NB_H)
+  void* fa_pan = nullptr;         // scratch panels, element type of F
   void* M = nullptr;            // X_t factors (double2 or float2), column-major f x k
   void* MT = nullptr;           // X_t^T, column-major k x f (backward sweep)
   void* Dinv = nullptr;         // 1/D (double2 or float2)
