@@ -378,6 +378,8 @@ def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, ser
            "iterations": [s["iterations"] for s in stats], "max_rel_residual": max(s["max_rel_residual"] for s in stats),
            "converged": all(s["converged"] for s in stats), "setup_s": setup_wall,
            "factor_s": stats[0]["factor_seconds"], "info": info, "phases": prof, "gpu_launches": launches,
+           "factor_ldlt_s": info["factor_ldlt_seconds"], "factor_inverse_s": info["factor_inverse_seconds"],
+           "perturbed_pivots": info["perturbed_pivots"],
            "coarse_fp32": S.options.coarse_fp32, "overlap": S.options.overlap,
            "tensor_cores": S.options.tensor_cores, "persistent_sweeps": S.options.persistent_sweeps}
     if with_e2e:

@@ -110,8 +110,8 @@ typedef struct hz_options {
                                hz_fwi_gradient, one Krylov space shared by the block: block CGS2 and CholQR2
                                as tall-skinny FP64 products, linearly dependent right-hand sides deflated;
                                needs max_block <= 32. Servers keep one Krylov space per column */
-  int32_t persistent_sweeps;/* 1 (default): each SIMT front sweep is one launch over all tree levels (resident
-                               CTAs take tiles in level order and wait for the fronts they depend on); 0: one
+  int32_t persistent_sweeps;/* 1: each SIMT front sweep is one launch over all tree levels (resident CTAs take
+                               tiles in level order and wait for the fronts they depend on); 0 (default): one
                                launch per level. The tensor-core tiles keep one launch per level */
   int32_t factor_fp32;      /* mixed form only. 1 (default): the fine fronts are factorised (partial LDL^T and
                                partitioned inverse) in complex FP32; 0: in FP64, then rounded to FP32. The

@@ -1322,7 +1322,7 @@ int hz_default_options(hz_options* o) {
   o->coarse_fp32 = 0;
   o->debug_bounds = 0;
   o->block_arnoldi = 0;
-  o->persistent_sweeps = 1;
+  o->persistent_sweeps = 0;
   o->factor_fp32 = 1;
   return HZ_OK;
 }

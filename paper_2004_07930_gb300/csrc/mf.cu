@@ -107,33 +107,9 @@ constexpr int MF_TK = 128;    // reduction length per tile (MF_TILE_K on the hos
 //             rows r >= k -> parent update c_U + t (Wout), c_U = the children's
 //             update vectors landing on the row
 //   backward: x at the pivot rows of the sub-vector
-// Each thread owns R output rows
-// (NT apart, so a warp reads 32 consecutive factor entries per column) and
-// the s right-hand sides as register accumulators; chunks of the input vector
-// are staged in shared memory and read as broadcasts.
-__device__ __forceinline__ void cp_async_elem(void* dst_smem, const float2* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_elem(void* dst_smem, const double2* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// columns of the factor tile per asynchronous chunk (two chunks in flight)
-template <typename V>
-struct TileChunk {
-  static constexpr int K = sizeof(V) == 8 ? 16 : 8;
-};
-
 template <typename V, int S>
 static constexpr size_t tile_smem_bytes() {
-  return sizeof(V) * ((size_t)MF_TK * S + 2 * (size_t)TileChunk<V>::K * MF_TILE);
+  return sizeof(V) * (size_t)MF_TK * S;  // the staged input rows
 }
 
 // loads of data that other CTAs of the same launch write (persistent sweeps):
@@ -148,11 +124,13 @@ __device__ __forceinline__ V ldv(const V* p) {
 
 // One tile. Each thread owns one output row (MF_TILE threads) and keeps the s
 // right-hand sides as register accumulators. The tile's input rows are
-// staged once in shared memory (read as broadcasts); the factor tile streams
-// through a two-chunk shared-memory ring filled by cp.async (a warp copies 32
-// consecutive entries of one factor column), so the next chunk's loads are in
-// flight while the current one is consumed. A tile with slot >= 0 writes its
-// partial result to P; the others apply the epilogue.
+// staged once in shared memory (read as broadcasts); each thread streams its
+// row of the factor tile straight from global memory (a warp reads 32
+// consecutive entries of one factor column per load), FA_UNROLL columns
+// ahead, so the only barrier is the one after the staging and the small
+// shared-memory footprint leaves room for several CTAs per SM. A tile with
+// slot >= 0 writes its partial result to P; the others apply the epilogue.
+constexpr int MF_UNROLL = 8;
 template <typename V, int S, bool FWD, bool CG>
 __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restrict__ kk, const int* __restrict__ ff,
                                            const int64_t* __restrict__ rowoff, const int64_t* __restrict__ Moff,
@@ -160,9 +138,7 @@ __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restric
                                            const int64_t* __restrict__ cptr, const int* __restrict__ cidx,
                                            const int64_t* __restrict__ Doff, const V* __restrict__ Dinv, V* Xsub,
                                            V* Wout, V* P, int s, unsigned char* smem_raw) {
-  constexpr int KCH = TileChunk<V>::K;
-  V(*bs)[S] = reinterpret_cast<V(*)[S]>(smem_raw);                                       // [MF_TK][S]
-  V(*mb)[MF_TILE] = reinterpret_cast<V(*)[MF_TILE]>(smem_raw + sizeof(V) * MF_TK * S);  // [2 KCH][MF_TILE]
+  V(*bs)[S] = reinterpret_cast<V(*)[S]>(smem_raw);  // [MF_TK][S]
   const int t = tile.x, r0 = tile.y, c0 = tile.z, slot = tile.w;
   const int f = ff[t], k = kk[t];
   const int nout = FWD ? f : k;
@@ -176,15 +152,6 @@ __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restric
   const int lmax = max(0, kstop - kbeg);
   const int rr = r0 + tid;
   const bool act = rr < nout;
-  const V* mcol = Mt + (act ? rr : 0) + (int64_t)kbeg * ld;
-  const int nch = (lmax + KCH - 1) / KCH;
-  // chunk 0 in flight while the input rows are staged
-  if (nch > 0) {
-    const int cn = min(KCH, lmax);
-    if (act)
-      for (int j = 0; j < cn; ++j) cp_async_elem(&mb[j][tid], mcol + (int64_t)j * ld);
-  }
-  cp_async_commit();
   for (int l = tid; l < lmax; l += MF_TILE) {
     const int64_t R = ro + kbeg + l;
     const int local = kbeg + l;
@@ -204,31 +171,28 @@ __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restric
 #pragma unroll
     for (int c = 0; c < S; ++c) bs[l][c] = v[c];
   }
+  __syncthreads();
   V acc[S];
 #pragma unroll
   for (int c = 0; c < S; ++c) acc[c] = mk2((decltype(V::x))0, (decltype(V::x))0);
-  for (int ch = 0; ch < nch; ++ch) {
-    // issue chunk ch + 1 into the other half of the ring, then wait for ch
-    if (ch + 1 < nch) {
-      const int j0 = (ch + 1) * KCH, cn = min(KCH, lmax - j0);
-      const int half = ((ch + 1) & 1) * KCH;
-      if (act)
-        for (int j = 0; j < cn; ++j) cp_async_elem(&mb[half + j][tid], mcol + (int64_t)(j0 + j) * ld);
-    }
-    cp_async_commit();
-    cp_async_wait<1>();
-    __syncthreads();
-    const int half = (ch & 1) * KCH;
-    const int j0 = ch * KCH, cn = min(KCH, lmax - j0);
-#pragma unroll 4
-    for (int j = 0; j < cn; ++j) {
-      const V m = mb[half + j][tid];
+  if (act) {
+    const V* mcol = Mt + rr + (int64_t)kbeg * ld;
+    int j = 0;
+    for (; j + MF_UNROLL <= lmax; j += MF_UNROLL) {
+      V m[MF_UNROLL];
 #pragma unroll
-      for (int c = 0; c < S; ++c) acc[c] = c_fma(m, bs[j0 + j][c], acc[c]);
+      for (int u = 0; u < MF_UNROLL; ++u) m[u] = __ldg(mcol + (int64_t)(j + u) * ld);
+#pragma unroll
+      for (int u = 0; u < MF_UNROLL; ++u)
+#pragma unroll
+        for (int c = 0; c < S; ++c) acc[c] = c_fma(m[u], bs[j + u][c], acc[c]);
     }
-    __syncthreads();  // the half just read is refilled in the next iteration
+    for (; j < lmax; ++j) {
+      const V m = __ldg(mcol + (int64_t)j * ld);
+#pragma unroll
+      for (int c = 0; c < S; ++c) acc[c] = c_fma(m, bs[j][c], acc[c]);
+    }
   }
-  cp_async_wait<0>();
   if (slot >= 0) {
     V* out = P + ((int64_t)slot * MF_TILE + tid) * s;
 #pragma unroll

@@ -6,7 +6,7 @@ right-hand sides of a block, block CGS2 + CholQR2 as tall-skinny products.
   1e-12 over the kept directions (the per-column form only orthogonalises
   each column's own Krylov vectors);
 * duplicated sources: the CholQR deflates the dependent directions, no NaN,
-  the duplicated columns are equal and converge;
+  the duplicated columns agree to rounding and converge;
 * the block form needs no more iterations than the per-column form.
 """
 import numpy as np
@@ -76,5 +76,5 @@ def test_block_duplicated_sources(cube):
         assert (res <= 1e-8).all()
         perm = dof_perm(S, space, 1000.0)
         assert rel_l2(u, u_or[:, perm]).max() <= 1e-6
-        np.testing.assert_array_equal(u[1], u[0])
-        np.testing.assert_array_equal(u[2], u[0])
+        # the duplicated columns share one Krylov direction; they agree to rounding
+        assert rel_l2(u[1], u[0]) <= 1e-12 and rel_l2(u[2], u[0]) <= 1e-12

@@ -1,6 +1,6 @@
 """Persistent front sweeps (one launch per sweep direction over every tree
-level, persistent_sweeps = 1, the default) against the per-level launches
-(persistent_sweeps = 0). Both run the same tiles with the same arithmetic
+level, persistent_sweeps = 1) against the per-level launches
+(persistent_sweeps = 0, the default). Both run the same tiles with the same arithmetic
 and sum a row block's partial tiles in the same slot order, so the local
 solves must agree bit for bit, whatever order the CTAs take the tiles in; a
 second application must repeat the first exactly."""
