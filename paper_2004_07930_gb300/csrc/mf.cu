@@ -152,6 +152,12 @@ __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restric
   const int lmax = max(0, kstop - kbeg);
   const int rr = r0 + tid;
   const bool act = rr < nout;
+  const V* mcol = Mt + (act ? rr : 0) + (int64_t)kbeg * ld;
+  // the first factor columns are read while the input rows are staged
+  V m0[MF_UNROLL];
+#pragma unroll
+  for (int u = 0; u < MF_UNROLL; ++u)
+    m0[u] = (act && u < lmax) ? __ldg(mcol + (int64_t)u * ld) : mk2((decltype(V::x))0, (decltype(V::x))0);
   for (int l = tid; l < lmax; l += MF_TILE) {
     const int64_t R = ro + kbeg + l;
     const int local = kbeg + l;
@@ -176,8 +182,13 @@ __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restric
 #pragma unroll
   for (int c = 0; c < S; ++c) acc[c] = mk2((decltype(V::x))0, (decltype(V::x))0);
   if (act) {
-    const V* mcol = Mt + rr + (int64_t)kbeg * ld;
-    int j = 0;
+    const int j0 = min(lmax, MF_UNROLL);
+#pragma unroll
+    for (int u = 0; u < MF_UNROLL; ++u)
+      if (u < j0)
+#pragma unroll
+        for (int c = 0; c < S; ++c) acc[c] = c_fma(m0[u], bs[u][c], acc[c]);
+    int j = j0;
     for (; j + MF_UNROLL <= lmax; j += MF_UNROLL) {
       V m[MF_UNROLL];
 #pragma unroll
