@@ -126,9 +126,11 @@ __device__ __forceinline__ V ldv(const V* p) {
 // right-hand sides as register accumulators. The tile's input rows are
 // staged once in shared memory (read as broadcasts); each thread streams its
 // row of the factor tile straight from global memory (a warp reads 32
-// consecutive entries of one factor column per load), FA_UNROLL columns
-// ahead, so the only barrier is the one after the staging and the small
-// shared-memory footprint leaves room for several CTAs per SM. A tile with
+// consecutive entries of one factor column per load), the next MF_UNROLL
+// columns in flight while the current ones are used (the first batch while
+// the input rows are staged), so the only barrier is the one after the
+// staging and the small shared-memory footprint leaves room for several CTAs
+// per SM. A tile with
 // slot >= 0 writes its partial result to P; the others apply the epilogue.
 constexpr int MF_UNROLL = 8;
 template <typename V, int S, bool FWD, bool CG>
@@ -182,26 +184,22 @@ __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restric
 #pragma unroll
   for (int c = 0; c < S; ++c) acc[c] = mk2((decltype(V::x))0, (decltype(V::x))0);
   if (act) {
-    const int j0 = min(lmax, MF_UNROLL);
-#pragma unroll
-    for (int u = 0; u < MF_UNROLL; ++u)
-      if (u < j0)
-#pragma unroll
-        for (int c = 0; c < S; ++c) acc[c] = c_fma(m0[u], bs[u][c], acc[c]);
-    int j = j0;
-    for (; j + MF_UNROLL <= lmax; j += MF_UNROLL) {
-      V m[MF_UNROLL];
-#pragma unroll
-      for (int u = 0; u < MF_UNROLL; ++u) m[u] = __ldg(mcol + (int64_t)(j + u) * ld);
+    // software pipeline: the next MF_UNROLL factor columns are in flight while the current ones are used
+    int j = 0;
+    while (j < lmax) {
+      const int jn = j + MF_UNROLL;
+      V m1[MF_UNROLL];
 #pragma unroll
       for (int u = 0; u < MF_UNROLL; ++u)
+        m1[u] = jn + u < lmax ? __ldg(mcol + (int64_t)(jn + u) * ld) : mk2((decltype(V::x))0, (decltype(V::x))0);
 #pragma unroll
-        for (int c = 0; c < S; ++c) acc[c] = c_fma(m[u], bs[j + u][c], acc[c]);
-    }
-    for (; j < lmax; ++j) {
-      const V m = __ldg(mcol + (int64_t)j * ld);
+      for (int u = 0; u < MF_UNROLL; ++u)
+        if (j + u < lmax)
 #pragma unroll
-      for (int c = 0; c < S; ++c) acc[c] = c_fma(m, bs[j][c], acc[c]);
+          for (int c = 0; c < S; ++c) acc[c] = c_fma(m0[u], bs[j + u][c], acc[c]);
+#pragma unroll
+      for (int u = 0; u < MF_UNROLL; ++u) m0[u] = m1[u];
+      j = jn;
     }
   }
   if (slot >= 0) {
