@@ -108,8 +108,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=["overthrust5", "overthrust5_quarter", "cube"], default="overthrust5",
-                    help="overthrust5_quarter: the 10 x 10 km corner of the same model (profiling case)")
+    ap.add_argument("--config", choices=["overthrust5", "overthrust5_quarter", "overthrust10", "cube"],
+                    default="overthrust5",
+                    help="overthrust5_quarter: the 10 x 10 km corner of the same model (profiling case); "
+                         "overthrust10: the same model at 10 Hz, 256 subdomains, 64 sources (mixed precision at scale)")
     ap.add_argument("--forms", default="mixed,fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the FP64 form")
@@ -120,6 +122,8 @@ def parse():
                          "paper_resolution (two- and one-level at 1.3 Hz on the same mesh: 5 P3 cells per "
                          "local wavelength as in the paper, coarse mesh at 2.5)")
     ap.add_argument("--maxit", type=int, default=500, help="FGMRES iteration cap (lower it only for profiling runs)")
+    ap.add_argument("--max-block", type=int, default=0,
+                    help="right-hand sides per block (0: the library default, 64; the 10 Hz workload needs 16 to fit)")
     ap.add_argument("--coarse", choices=["gmres", "none", "direct"], default="gmres",
                     help="coarse level of the headline forms (the paper's: gmres, 10 inner steps)")
     ap.add_argument("--tensor-cores", type=int, choices=[-1, 0, 1], default=-1,
@@ -165,6 +169,12 @@ def problem(cfg):
         nx, ny, nz = p["fine"]["ncells"]
         return p, ("Overthrust-like 5 Hz, 10x10 km corner crop, %dx%dx%d cells, 16 subdomains, %d sources"
                    % (nx, ny, nz, len(p["src_xyz"])))
+    if cfg == "overthrust10":
+        p = wl.overthrust_problem(10.0, nparts=256, seed=0,
+                                  sources=wl.surface_source_grid(8, 8, 1250.0, 18750.0))
+        nx, ny, nz = p["fine"]["ncells"]
+        return p, ("Overthrust-like 20x20x4.65 km, 10 Hz, %dx%dx%d cells x 6 Kuhn tets, P3, 256 subdomains "
+                   "(16x16x1), overlap 1, nested coarse mesh, 64 surface sources (8x8 grid)" % (nx, ny, nz))
     p = wl.overthrust_problem(5.0, nparts=64, seed=0)
     nx, ny, nz = p["fine"]["ncells"]
     return p, ("Overthrust-like 20x20x4.65 km, 5 Hz, %dx%dx%d cells x 6 Kuhn tets, P3, 64 subdomains "
@@ -344,6 +354,8 @@ def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, ser
         opts["tensor_cores"] = TENSOR_CORES
     if PERSISTENT >= 0:
         opts["persistent_sweeps"] = PERSISTENT
+    if MAX_BLOCK > 0:
+        opts["max_block"] = MAX_BLOCK
     t0 = time.time()
     S = hz.Solver.from_problem(prob, precision=prec, rtol=1e-6, stream=stream, maxit=MAXIT, **opts)
     setup_wall = time.time() - t0
@@ -381,7 +393,8 @@ def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, ser
            "factor_ldlt_s": info["factor_ldlt_seconds"], "factor_inverse_s": info["factor_inverse_seconds"],
            "perturbed_pivots": info["perturbed_pivots"],
            "coarse_fp32": S.options.coarse_fp32, "overlap": S.options.overlap,
-           "tensor_cores": S.options.tensor_cores, "persistent_sweeps": S.options.persistent_sweeps}
+           "tensor_cores": S.options.tensor_cores, "persistent_sweeps": S.options.persistent_sweeps,
+           "max_block": S.options.max_block, "device_gb": S.info()["device_bytes"] / 1e9}
     if with_e2e:
         import numpy as np
 
@@ -407,6 +420,7 @@ def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, ser
 MAXIT = 500
 TENSOR_CORES = -1
 PERSISTENT = -1
+MAX_BLOCK = 0
 
 
 def run_spmm_sweep(args):
@@ -507,9 +521,61 @@ def run_serving(args):
         S.close()
 
 
+def run_scale(args):
+    """Mixed precision at scale: the 10 Hz workload (256 subdomains, 64
+    sources in blocks of --max-block), one-level ORAS (at 1.3 P3 cells per
+    wavelength the coarse level slows FGMRES down). Reports RHS/s of the mixed
+    form, its iterations and device footprint, and the relative L2 difference
+    to the FP64 form on the first 4 sources (the FP64 form runs at the GPU's
+    FP64 rate, so it solves only those)."""
+    import numpy as np
+    import torch
+
+    from paper_2004_07930_gb300 import hz
+
+    torch.cuda.set_device(0)
+    hz.load()
+    prob, desc = problem("overthrust10")
+    src = prob["src_xyz"]
+    mb = args.max_block if args.max_block > 0 else 16
+    opts = dict(rtol=1e-6, maxit=args.maxit, coarse_mode=hz.HZ_COARSE_NONE, max_block=mb)
+    out = {"mode": "scale", "metric": "RHS solved/s at rtol 1e-6", "unit": "RHS/s", "n_gpus": 1,
+           "config": {"workload": desc, "preconditioner": "one-level ORAS", "max_block": mb}}
+    clocks = ClockSampler(0)
+    t0 = time.time()
+    S = hz.Solver.from_problem(prob, precision=hz.HZ_PREC_MIXED, **opts)
+    out["setup_s"] = time.time() - t0
+    info = S.info()
+    out["config"].update({"n": info["n"], "nnz": info["nnz"], "factor_entries": info["factor_entries"],
+                          "factor_ldlt_s": info["factor_ldlt_seconds"], "factor_inverse_s": info["factor_inverse_seconds"]})
+    S.solve(src[:mb], raise_on_notconv=False)  # warm-up block
+    clocks.start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    u_mixed, st = S.solve(src, raise_on_notconv=False)
+    e1.record()
+    torch.cuda.synchronize()
+    out["clocks"] = clocks.stop()
+    sec = e0.elapsed_time(e1) / 1e3
+    out.update({"value": len(src) / sec, "seconds": sec, "iterations": st["iterations"],
+                "converged": st["converged"], "max_rel_residual": st["max_rel_residual"],
+                "device_gb": S.info()["device_bytes"] / 1e9})
+    S.close()
+    t0 = time.time()
+    with hz.Solver.from_problem(prob, precision=hz.HZ_PREC_FP64, **opts) as S64:
+        u64, st64 = S64.solve(src[:4], raise_on_notconv=False)
+        out["fp64"] = {"sources": 4, "seconds_incl_setup": time.time() - t0, "iterations": st64["iterations"],
+                       "converged": st64["converged"]}
+    d = np.linalg.norm(u_mixed[:4] - u64, axis=1) / np.linalg.norm(u64, axis=1)
+    out["mixed_vs_fp64_rel_l2"] = float(d.max())
+    print(json.dumps(out), flush=True)
+
+
 def main():
-    global MAXIT, TENSOR_CORES, PERSISTENT
+    global MAXIT, TENSOR_CORES, PERSISTENT, MAX_BLOCK
     args = parse()
+    MAX_BLOCK = args.max_block
     MAXIT = args.maxit
     TENSOR_CORES = args.tensor_cores
     PERSISTENT = args.persistent
@@ -521,6 +587,9 @@ def main():
         return
     if args.spmm_sweep:
         run_spmm_sweep(args)
+        return
+    if args.config == "overthrust10":
+        run_scale(args)
         return
     ws, rank, local = dist_env()
     import torch
@@ -616,7 +685,8 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype,
         "data": "synthetic (seeded Overthrust-like model; no real data)",
-        "config": {"workload": desc, "n": r["info"]["n"], "nnz": r["info"]["nnz"], "sources_per_step": 16,
+        "config": {"workload": desc, "n": r["info"]["n"], "nnz": r["info"]["nnz"],
+                   "sources_per_step": len(prob["src_xyz"]), "max_block": r.get("max_block"),
                    "rtol": 1e-6, "preconditioner": {"gmres": "two-level ORAS, coarse by 10 GMRES steps",
                                                     "none": "one-level ORAS", "direct": "two-level ORAS, direct coarse"}[args.coarse],
                    "l2_flush": "inputs larger than L2 (factors %.1f GB)" %

@@ -66,3 +66,27 @@ def test_crop_one_level_wavefield_matches_oracle(crop):
         perm = dof_perm(S, space, 20000.0)
         u, st = S.solve(p["src_xyz"])
         assert rel_l2(u, u_or[:, perm]).max() <= 1e-5
+
+
+@pytest.fixture(scope="module")
+def crop10():
+    """8 x 8 cells (1.4 x 1.4 km, full depth) of the 10 Hz workload: the
+    oracle's share of the mixed-precision-at-scale configuration (a 1/8-volume
+    crop, ~0.75M dofs, is beyond a direct solve on the host)."""
+    torch_cuda()
+    p = wl.overthrust_problem(10.0, nparts=4, crop=(0.07, 0.07, 1.0), sources=[[700.0, 600.0, 100.0]])
+    space, A, F = oa.system(p["fine"], p["velocity"], p["freq"], p["src_xyz"])
+    return p, space, oa.solve(A, F)
+
+
+@pytest.mark.parametrize("precision,bound", [(hz.HZ_PREC_FP64, 2e-6), (hz.HZ_PREC_MIXED, 1e-5)])
+def test_crop_10hz_wavefield_matches_oracle(crop10, precision, bound):
+    p, space, u_or = crop10
+    assert p["fine"]["ncells"][:2] == (8, 8)
+    with hz.Solver.from_problem(p, precision=precision, rtol=1e-6) as S:
+        perm = dof_perm(S, space, 20000.0)
+        u, st = S.solve(p["src_xyz"])
+        err = rel_l2(u, u_or[:, perm])
+        print("10 Hz crop n", space.n, "precision", precision, "iterations", st["iterations"], "rel L2", err)
+        assert st["converged"] == 1
+        assert err.max() <= bound
