@@ -525,13 +525,16 @@ def run_scale(args):
     """Mixed precision at scale: the 10 Hz workload (256 subdomains, 64
     sources in blocks of --max-block), one-level ORAS (at 1.3 P3 cells per
     wavelength the coarse level slows FGMRES down). Reports RHS/s of the mixed
-    form, its iterations and device footprint, and the relative L2 difference
-    to the FP64 form on the first 4 sources (the FP64 form runs at the GPU's
-    FP64 rate, so it solves only those)."""
+    form, its iterations and device footprint. The FP64 form of the full
+    10 Hz problem does not fit the device (its frontal workspace alone is
+    ~384 GB of complex FP64), so the mixed-vs-FP64 difference is measured on a
+    corner crop of the same 10 Hz model (a quarter of each horizontal axis,
+    16 subdomains, 4 sources), both forms on the GPU."""
     import numpy as np
     import torch
 
     from paper_2004_07930_gb300 import hz
+    from paper_2004_07930_gb300 import workloads as wl
 
     torch.cuda.set_device(0)
     hz.load()
@@ -547,7 +550,8 @@ def run_scale(args):
     out["setup_s"] = time.time() - t0
     info = S.info()
     out["config"].update({"n": info["n"], "nnz": info["nnz"], "factor_entries": info["factor_entries"],
-                          "factor_ldlt_s": info["factor_ldlt_seconds"], "factor_inverse_s": info["factor_inverse_seconds"]})
+                          "max_front": info["max_front"], "factor_ldlt_s": info["factor_ldlt_seconds"],
+                          "factor_inverse_s": info["factor_inverse_seconds"]})
     S.solve(src[:mb], raise_on_notconv=False)  # warm-up block
     clocks.start()
     torch.cuda.synchronize()
@@ -562,14 +566,26 @@ def run_scale(args):
                 "converged": st["converged"], "max_rel_residual": st["max_rel_residual"],
                 "device_gb": S.info()["device_bytes"] / 1e9})
     S.close()
-    t0 = time.time()
-    with hz.Solver.from_problem(prob, precision=hz.HZ_PREC_FP64, **opts) as S64:
-        u64, st64 = S64.solve(src[:4], raise_on_notconv=False)
-        out["fp64"] = {"sources": 4, "seconds_incl_setup": time.time() - t0, "iterations": st64["iterations"],
-                       "converged": st64["converged"]}
-    d = np.linalg.norm(u_mixed[:4] - u64, axis=1) / np.linalg.norm(u64, axis=1)
-    out["mixed_vs_fp64_rel_l2"] = float(d.max())
+    del u_mixed
     print(json.dumps(out), flush=True)
+    # mixed vs FP64 on a corner crop of the same 10 Hz model
+    crop = wl.overthrust_problem(10.0, nparts=16, seed=0, crop=(0.25, 0.25, 1.0),
+                                 sources=wl.surface_source_grid(2, 2, 1250.0, 3750.0))
+    cmp_ = {"crop": "10 Hz, (0.25, 0.25, 1) corner crop, %dx%dx%d cells, 16 subdomains, 4 sources"
+            % tuple(crop["fine"]["ncells"])}
+    copts = dict(opts, max_block=4)
+    u = {}
+    for name, prec in (("mixed", hz.HZ_PREC_MIXED), ("fp64", hz.HZ_PREC_FP64)):
+        t0 = time.time()
+        with hz.Solver.from_problem(crop, precision=prec, **copts) as Sc:
+            t1 = time.time()
+            u[name], stc = Sc.solve(crop["src_xyz"], raise_on_notconv=False)
+            cmp_[name] = {"setup_s": t1 - t0, "solve_s": time.time() - t1, "iterations": stc["iterations"],
+                          "converged": stc["converged"], "max_rel_residual": stc["max_rel_residual"],
+                          "device_gb": Sc.info()["device_bytes"] / 1e9, "n": Sc.n}
+    d = np.linalg.norm(u["mixed"] - u["fp64"], axis=1) / np.linalg.norm(u["fp64"], axis=1)
+    cmp_["mixed_vs_fp64_rel_l2"] = float(d.max())
+    print(json.dumps({"mode": "scale_crop_fp64", **cmp_}), flush=True)
 
 
 def main():

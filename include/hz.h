@@ -116,6 +116,14 @@ typedef struct hz_options {
   int32_t factor_fp32;      /* mixed form only. 1 (default): the fine fronts are factorised (partial LDL^T and
                                partitioned inverse) in complex FP32; 0: in FP64, then rounded to FP32. The
                                coarse fronts are factorised in FP64 in both forms */
+  int32_t recycle;          /* Krylov subspace recycling (deflated restarting across cycles and solves, in the
+                               spirit of GCRO-DR; the paper's outlook on reusing Krylov information across
+                               sources). k in [1, 16]: after every FGMRES cycle the k/2 harmonic Ritz vectors
+                               of smallest magnitude of the slowest column's cycle join a space U of at most k
+                               vectors, kept by the context for every later solve of the same operator; C = A U
+                               is kept orthonormal, each cycle starts from x += U C^H r and its Arnoldi runs on
+                               (I - C C^H) A M^{-1}. 0 (default): off. Needs per-column FGMRES (block_arnoldi 0)
+                               and restart >= 2; servers do not recycle. Costs 6 k n complex FP64 of device memory */
 } hz_options;
 
 typedef struct hz_stats {

@@ -25,6 +25,12 @@
 #include "dd_host.h"
 #include "kernels.cuh"
 
+namespace hz {
+// harmonic Ritz vectors of an FGMRES cycle (ritz_host.cpp)
+bool harmonic_ritz(const std::vector<std::complex<double>>& Hbar, int m, int k,
+                   std::vector<std::complex<double>>& P, std::vector<std::complex<double>>& theta);
+}  // namespace hz
+
 using namespace hz;
 
 namespace {
@@ -742,6 +748,11 @@ struct hz_ctx {
   float2 *v32 = nullptr, *q32 = nullptr, *t32 = nullptr;  // FP32 preconditioner blocks (mixed form)
   DevKrylov Kout, Kin;
   DevBlockKrylov Bk;          // block FGMRES (option block_arnoldi), on Kout's basis arrays
+  // Krylov subspace recycling (option recycle): rk_eff vectors U, C = A U (orthonormal), [n][rk_eff]
+  int rk_eff = 0;
+  double2 *Ur = nullptr, *Cr = nullptr, *Un = nullptr, *Cn = nullptr, *Rt1 = nullptr, *Rt2 = nullptr;
+  double2 *Rsm = nullptr, *Rp = nullptr;   // device k x k factors / coefficients (small)
+  double2 *Bc = nullptr, *Yr = nullptr, *Rpart = nullptr;  // per block: [m][rk][s], [rk][s], partial sums
   double* bnorm = nullptr;
   double* rnorm = nullptr;
   double* h_res = nullptr;    // pinned host
@@ -816,6 +827,13 @@ void ensure_workspace(hz_ctx* c, int s) {
   c->lf.mf.P = p.alloc<char>((size_t)std::max(c->lf.mf.max_slots, c->lf.mf.pslots) * MF_TILE_ROWS * s * ef);
   c->lf.mf.s_cap = s;
   alloc_krylov(c->Kout, n, s, c->opt.restart, p, false);
+  if (c->opt.recycle > 0) {
+    const int rk = c->opt.recycle, m = c->opt.restart;
+    c->Kout.Hraw = p.alloc<double2>((size_t)s * (m + 1) * m);
+    c->Bc = p.alloc<double2>((size_t)m * rk * s);
+    c->Yr = p.alloc<double2>((size_t)rk * std::max(s, rk));
+    c->Rpart = p.alloc<double2>((size_t)c->Kout.nblk * rk * std::max(s, rk));
+  }
   if (c->opt.block_arnoldi) {
     DevBlockKrylov& B = c->Bk;
     const int m = c->opt.restart;
@@ -1074,19 +1092,27 @@ void apply_prec(hz_ctx* c, const double2* V, double2* Zout, int s) {
 // current residual c->R, at most max_its iterations (fewer when every column
 // has converged or broken down), then X += Zk y. K.tol must hold the
 // per-column absolute tolerances. Returns the iterations done.
-int fgmres_cycle(hz_ctx* c, int s, int max_its) {
+void check_launch();
+
+int fgmres_cycle(hz_ctx* c, int s, int max_its, bool recyc = false) {
   cudaStream_t st = c->st;
   const int64_t n = c->space.n;
   DevKrylov& K = c->Kout;
   K.s = s;
   const int m = std::min(c->opt.restart, max_its);
   const int64_t vs = n * s;
+  const int rk = recyc ? c->rk_eff : 0;  // recycled directions projected out of every A z
   krylov_start(K, c->R, st);
   int its = 0;
   for (int j = 0; j < m; ++j) {
     apply_prec(c, (double2*)K.V + j * vs, (double2*)K.Zk + j * vs, s);
     spmm_A(c, (double2*)K.Zk + j * vs, (double2*)K.W, nullptr, s, 0);
     int id = c->prof.begin(PH_ARNOLDI, st);
+    if (rk > 0) {  // B_j = C^H w, w -= C B_j
+      double2* Bj = c->Bc + (size_t)j * rk * s;
+      recycle_dot(c->Cr, rk, (double2*)K.W, s, n, c->Rpart, K.nblk, Bj, st);
+      recycle_axpy(c->Cr, rk, Bj, (double2*)K.W, s, n, -1.0, st);
+    }
     krylov_arnoldi(K, j, st);
     // two CGS passes (dots + update) over V_0..j and W, a norm and a scale
     c->prof.end(id, st, 2.0 * 2.0 * 8.0 * n * (j + 1) * s, 16.0 * n * s * (4.0 * (j + 1) + 6.0));
@@ -1098,7 +1124,95 @@ int fgmres_cycle(hz_ctx* c, int s, int max_its) {
     if (alldone) break;
   }
   krylov_update(K, c->X, st);
+  if (rk > 0) {  // x -= U sum_j B_j y_j
+    recycle_corr(c->Bc, K.y, K.kc, rk, s, K.m, c->Yr, st);
+    recycle_axpy(c->Ur, rk, c->Yr, c->X, s, n, -1.0, st);
+  }
   return its;
+}
+
+// Recycling, start of a cycle: x += U C^H r, r -= C C^H r for every column.
+void recycle_project(hz_ctx* c, int s) {
+  const int rk = c->rk_eff;
+  if (rk == 0) return;
+  const int64_t n = c->space.n;
+  recycle_dot(c->Cr, rk, c->R, s, n, c->Rpart, c->Kout.nblk, c->Yr, c->st);
+  recycle_axpy(c->Ur, rk, c->Yr, c->X, s, n, 1.0, c->st);
+  recycle_axpy(c->Cr, rk, c->Yr, c->R, s, n, -1.0, c->st);
+}
+
+// Cholesky R^H R = G of a small Hermitian matrix (row-major, k x k); false if
+// a pivot is not clearly positive
+static bool small_cholesky(const std::vector<double2>& G, int k, std::vector<double2>& R) {
+  R.assign((size_t)k * k, make_double2(0.0, 0.0));
+  double gmax = 0.0;
+  for (int j = 0; j < k; ++j) gmax = std::max(gmax, G[j * k + j].x);
+  for (int j = 0; j < k; ++j) {
+    double d = G[j * k + j].x;
+    for (int q = 0; q < j; ++q) d -= R[q * k + j].x * R[q * k + j].x + R[q * k + j].y * R[q * k + j].y;
+    if (!(d > 1e-12 * gmax)) return false;
+    const double rjj = std::sqrt(d);
+    R[j * k + j] = make_double2(rjj, 0.0);
+    for (int l = j + 1; l < k; ++l) {
+      cplx v(G[j * k + l].x, G[j * k + l].y);
+      for (int q = 0; q < j; ++q) v -= std::conj(cplx(R[q * k + j].x, R[q * k + j].y)) * cplx(R[q * k + l].x, R[q * k + l].y);
+      R[j * k + l] = make_double2(v.real() / rjj, v.imag() / rjj);
+    }
+  }
+  return true;
+}
+
+// Recycling, end of a cycle: harmonic Ritz vectors of the slowest column's
+// cycle give knew new directions U_new = Z P; they join the kept ones (the
+// oldest beyond the option's k are dropped) and C = A U is orthonormalised
+// by two Cholesky QR passes, U transformed alike. A failed step keeps the
+// previous space.
+void recycle_update(hz_ctx* c, int s, const std::vector<int>& kc) {
+  const int RK = c->opt.recycle, m = c->opt.restart;
+  const int64_t n = c->space.n;
+  cudaStream_t st = c->st;
+  int col = 0;
+  for (int q = 1; q < s; ++q)
+    if (kc[q] > kc[col]) col = q;
+  const int me = kc[col];
+  const int knew = std::min(std::max(1, RK / 2), me - 1);
+  if (knew < 1) return;
+  std::vector<double2> hraw((size_t)(m + 1) * m);
+  CK(cudaMemcpyAsync(hraw.data(), c->Kout.Hraw + (size_t)col * (m + 1) * m, hraw.size() * sizeof(double2),
+                     cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<cplx> Hb((size_t)(me + 1) * me, cplx(0, 0)), P, theta;
+  for (int j = 0; j < me; ++j)
+    for (int i = 0; i <= std::min(j + 1, me); ++i)
+      Hb[i + (size_t)j * (me + 1)] = cplx(hraw[i + (size_t)j * (m + 1)].x, hraw[i + (size_t)j * (m + 1)].y);
+  if (!harmonic_ritz(Hb, me, knew, P, theta)) return;
+  std::vector<double2> Pd(P.size());
+  for (size_t i = 0; i < P.size(); ++i) Pd[i] = make_double2(P[i].real(), P[i].imag());
+  CK(cudaMemcpyAsync(c->Rp, Pd.data(), Pd.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+  const int total = std::min(RK, c->rk_eff + knew), kold = total - knew;
+  // new directions and their images: Rt1 = Z P, Rt2 = A Rt1 ([n][knew])
+  recycle_build((const double2*)c->Kout.Zk, n * s, s, col, c->Rp, me, knew, c->Rt1, knew, 0, n, st);
+  spmm_split(c->A, c->Rt1, c->Rt2, nullptr, knew, 0, st);
+  recycle_copy(c->Rt1, knew, 0, c->Un, total, 0, knew, n, st);
+  recycle_copy(c->Rt2, knew, 0, c->Cn, total, 0, knew, n, st);
+  if (kold > 0) {
+    recycle_copy(c->Ur, c->rk_eff, 0, c->Un, total, knew, kold, n, st);
+    recycle_copy(c->Cr, c->rk_eff, 0, c->Cn, total, knew, kold, n, st);
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    recycle_dot(c->Cn, total, c->Cn, total, n, c->Rpart, c->Kout.nblk, c->Rsm, st);
+    std::vector<double2> G((size_t)total * total), R;
+    CK(cudaMemcpyAsync(G.data(), c->Rsm, G.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (!small_cholesky(G, total, R)) return;  // keep the previous space
+    CK(cudaMemcpyAsync(c->Rsm, R.data(), R.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+    recycle_trsm(c->Cn, n, total, c->Rsm, st);
+    recycle_trsm(c->Un, n, total, c->Rsm, st);
+  }
+  check_launch();
+  std::swap(c->Ur, c->Un);
+  std::swap(c->Cr, c->Cn);
+  c->rk_eff = total;
 }
 
 // One restart cycle of block FGMRES (option block_arnoldi): one Krylov space
@@ -1166,12 +1280,16 @@ int fgmres(hz_ctx* c, int s, hz_stats* stats) {
   double maxrel = 0.0;
   std::vector<int> col_its(s, 0), kc(s);
   const bool block = c->opt.block_arnoldi != 0;
+  const bool recyc = !block && c->opt.recycle > 0;
   while (true) {
-    const int done_its = block ? fgmres_cycle_block(c, s, c->opt.maxit - its) : fgmres_cycle(c, s, c->opt.maxit - its);
+    if (recyc) recycle_project(c, s);
+    const int done_its =
+        block ? fgmres_cycle_block(c, s, c->opt.maxit - its) : fgmres_cycle(c, s, c->opt.maxit - its, recyc);
     its += done_its;
     if (!block) CK(cudaMemcpyAsync(kc.data(), K.kc, s * sizeof(int), cudaMemcpyDeviceToHost, st));
     true_residual(c, s);  // synchronises the stream
     for (int q = 0; q < s; ++q) col_its[q] += block ? done_its : kc[q];
+    if (recyc) recycle_update(c, s, kc);
     all_conv = true;
     maxrel = 0.0;
     for (int q = 0; q < s; ++q) {
@@ -1324,6 +1442,7 @@ int hz_default_options(hz_options* o) {
   o->block_arnoldi = 0;
   o->persistent_sweeps = 0;
   o->factor_fp32 = 1;
+  o->recycle = 0;
   return HZ_OK;
 }
 
@@ -1350,6 +1469,8 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
     if (o.overlap < 1 || o.overlap > 16) throw HzError{HZ_EINVAL, "overlap must be in [1, 16]"};
     if (o.block_arnoldi != 0 && (o.block_arnoldi != 1 || o.max_block > 32))
       throw HzError{HZ_EINVAL, "block_arnoldi needs max_block <= 32"};
+    if (o.recycle < 0 || o.recycle > 16 || (o.recycle > 0 && (o.block_arnoldi || o.restart < 2)))
+      throw HzError{HZ_EINVAL, "recycle must be in [0, 16], with per-column FGMRES and restart >= 2"};
     mesh_from_abi(fine, c->fine);
     mesh_build_adjacency(c->fine);
     const int64_t ne = c->fine.ne;
@@ -1432,6 +1553,17 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
     if (o.pivot_tau == 0.0 && c->perturbed) throw HzError{HZ_ESINGULAR, "zero pivot in a local factorisation"};
     if (o.debug_bounds) {
       check_bounds(c.get());
+    }
+    if (o.recycle > 0) {  // recycled space: lives as long as the context (valid for its A)
+      const int64_t n = c->space.n, rk = o.recycle;
+      c->Ur = c->pool.alloc<double2>(n * rk);
+      c->Cr = c->pool.alloc<double2>(n * rk);
+      c->Un = c->pool.alloc<double2>(n * rk);
+      c->Cn = c->pool.alloc<double2>(n * rk);
+      c->Rt1 = c->pool.alloc<double2>(n * rk);
+      c->Rt2 = c->pool.alloc<double2>(n * rk);
+      c->Rsm = c->pool.alloc<double2>(rk * rk);
+      c->Rp = c->pool.alloc<double2>((int64_t)o.restart * rk);
     }
     // address of the allocation-free product's scratch on this device (loads it here)
     hz::noalloc_scratch_address(&c->noalloc_scratch);

@@ -194,8 +194,23 @@ struct DevKrylov {
   int* kc = nullptr;        // [s] accepted Arnoldi steps
   int* done = nullptr;      // [s]
   int* reorth = nullptr;    // [s] second Gram-Schmidt pass needed
+  double2* Hraw = nullptr;  // [s][(m+1) m] unrotated Hessenberg (recycling only; may be NULL)
   int nblk = 0;
 };
+
+// --- Krylov subspace recycling (option recycle): k vectors U shared by all columns,
+// C = A U orthonormal; blocks [n][k] row-major ---
+void recycle_dot(const double2* Cb, int k, const double2* W, int s, int64_t n, double2* part, int nblk, double2* out,
+                 cudaStream_t st);  // out[a][c] = sum_r conj(C[r][a]) W[r][c]
+void recycle_axpy(const double2* Cb, int k, const double2* Y, double2* W, int s, int64_t n, double alpha,
+                  cudaStream_t st);  // W[r][c] += alpha sum_a C[r][a] Y[a][c]
+void recycle_corr(const double2* Bc, const double2* y, const int* kc, int k, int s, int m, double2* T,
+                  cudaStream_t st);  // T[a][c] = sum_{j < kc[c]} Bc[j][a][c] y[c][j]
+void recycle_build(const double2* Zk, int64_t vstride, int s, int col, const double2* P, int m, int knew,
+                   double2* U, int k, int q0, int64_t n, cudaStream_t st);  // U[r][q0+q] = sum_j Zk_j[r][col] P[j + q m]
+void recycle_trsm(double2* W, int64_t n, int k, const double2* R, cudaStream_t st);  // W <- W R^{-1} (R k x k upper, row-major)
+void recycle_copy(const double2* src, int sk, int s0, double2* dst, int dk, int d0, int count, int64_t n,
+                  cudaStream_t st);  // dst[r][d0 + q] = src[r][s0 + q]
 
 // --- block Krylov (one Krylov space shared by the s columns; FP64, s <= 32) ---
 struct DevBlockKrylov {

@@ -183,7 +183,7 @@ __global__ void k_arnoldi_finish(int s, int m, int j, const double2* __restrict_
                                  const double2* __restrict__ nrm2, double2* __restrict__ H, double* __restrict__ cs,
                                  double2* __restrict__ sn, double2* __restrict__ g, double* __restrict__ beta,
                                  const double* __restrict__ tol, int* __restrict__ kc, int* __restrict__ done,
-                                 double* __restrict__ res) {
+                                 double* __restrict__ res, double2* __restrict__ Hraw) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= s) return;
   const double hb = sqrt(nrm2[c].x);
@@ -195,6 +195,10 @@ __global__ void k_arnoldi_finish(int s, int m, int j, const double2* __restrict_
   double2* Hc = H + (int64_t)c * (m + 1) * m + (int64_t)j * (m + 1);
   for (int i = 0; i <= j; ++i) Hc[i] = zadd(h1[i * s + c], h2[i * s + c]);
   Hc[j + 1] = make_double2(breakdown ? 0.0 : hb, 0.0);
+  if (Hraw) {  // the unrotated column (recycling reads it after the cycle)
+    double2* Hr = Hraw + (int64_t)c * (m + 1) * m + (int64_t)j * (m + 1);
+    for (int i = 0; i <= j + 1; ++i) Hr[i] = Hc[i];
+  }
   double* csc = cs + c * m;
   double2* snc = sn + c * m;
   for (int i = 0; i < j; ++i) {
@@ -290,7 +294,7 @@ static void krylov_arnoldi_t(DevKrylov& K, int j, cudaStream_t st) {
   { k_update<V><<<gr, 256, 0, st>>>(Vb, vs, j + 1, K.h2, W, K.n, K.s, K.reorth); count_launch(); }
   mdot<V>(K, W, 0, 1, W, nrm, st);
   { k_arnoldi_finish<<<1, 64, 0, st>>>(K.s, K.m, j, K.h1, K.h2, nrm, K.H, K.cs, K.sn, K.g, K.beta, K.tol, K.kc, K.done,
-                                     K.res); count_launch(); }
+                                     K.res, K.Hraw); count_launch(); }
   { k_scale_cols<V><<<gr, 256, 0, st>>>(W, K.beta, Vb + (int64_t)(j + 1) * vs, K.n, K.s); count_launch(); }
 }
 

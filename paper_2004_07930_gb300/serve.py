@@ -27,9 +27,15 @@ from . import hz
 
 def slots_for_budget(solvers, device_budget, max_slots=64):
     """Slots per frequency: an equal share of `device_budget` bytes divided by
-    the bytes of one column on that frequency's solver (at least 1)."""
+    the bytes of one column on that frequency's solver, rounded down to a
+    power of two (the kernels run the instantiation for the next power of two
+    of the block width, so other widths pay for idle columns), at least 1."""
     share = float(device_budget) / len(solvers)
-    return {f: int(max(1, min(max_slots, share // S.column_bytes()))) for f, S in solvers.items()}
+    out = {}
+    for f, S in solvers.items():
+        n = int(max(1, min(max_slots, share // S.column_bytes())))
+        out[f] = 1 << (n.bit_length() - 1)
+    return out
 
 
 class ServingLoop:

@@ -38,6 +38,7 @@ def test_default_options(lib):
     assert o.rtol == 1e-6 and o.restart == 30 and o.max_block == 64 and o.coarse_inner_its == 10
     assert o.coarse_mode == hz.HZ_COARSE_GMRES
     assert o.overlap == 1 and o.coarse_fp32 == 0 and o.debug_bounds == 0 and o.tensor_cores == 0
+    assert o.recycle == 0
 
 
 def _setup_rc(prob, part=None, nparts=None, vel=None, freq=None, **opts):
@@ -68,6 +69,10 @@ def test_setup_rejects_bad_inputs(lib):
     assert _setup_rc(p, overlap=0) == hz.HZ_EINVAL
     assert _setup_rc(p, overlap=17) == hz.HZ_EINVAL
     assert _setup_rc(p, block_arnoldi=1, max_block=64) == hz.HZ_EINVAL     # block FGMRES: max_block <= 32
+    assert _setup_rc(p, recycle=17) == hz.HZ_EINVAL                        # recycled space: at most 16 vectors
+    assert _setup_rc(p, recycle=-1) == hz.HZ_EINVAL
+    assert _setup_rc(p, recycle=4, block_arnoldi=1, max_block=16) == hz.HZ_EINVAL  # per-column FGMRES only
+    assert _setup_rc(p, recycle=4, restart=1) == hz.HZ_EINVAL
     assert "partition" in hz.load().hz_last_error().decode() or True
     assert lib.hz_strerror(hz.HZ_ENOTCONV).decode() == "not converged"
 

@@ -104,7 +104,7 @@ def test_server_rejects_bad_requests():
 
 def test_admission_by_device_budget():
     """A budget of 2.5 columns' worth of device bytes gives the server 2
-    slots: a third source waits in the queue and is admitted when a slot (and
+    slots (the power of two below 2.5): a third source waits in the queue and is admitted when a slot (and
     its memory) frees; every request still matches the oracle."""
     torch_cuda()
     p = wl.cube_problem(ncell=4)

@@ -83,7 +83,7 @@ def test_slots_from_device_budget(monkeypatch):
     monkeypatch.setattr(serve.hz, "Server", FakeServer)
     solvers = {3.5: FakeSolver(1e8), 5.0: FakeSolver(3e8), 7.0: FakeSolver(5e10)}
     loop = serve.ServingLoop(solvers, device_budget=6e9)
-    assert loop.slots == {3.5: 20, 5.0: 6, 7.0: 1}
-    assert loop.servers[5.0].slots == 6
+    assert loop.slots == {3.5: 16, 5.0: 4, 7.0: 1}          # 20, 6, 1 columns fit; powers of two
+    assert loop.servers[5.0].slots == 4
     big = serve.slots_for_budget({1.0: FakeSolver(1.0)}, 1e12)
     assert big == {1.0: 64}
