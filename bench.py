@@ -130,6 +130,8 @@ def parse():
                     help="mixed form: front sweeps on the tcgen05 tensor cores (1) or SIMT (0); -1: library default")
     ap.add_argument("--persistent", type=int, choices=[-1, 0, 1], default=-1,
                     help="SIMT front sweeps as one launch per direction (1) or one per level (0); -1: library default")
+    ap.add_argument("--emulate-fp64", type=int, choices=[-1, 0, 1], default=-1,
+                    help="mixed form: FP64 products and Arnoldi as FP32 pairs (1) or native FP64 (0); -1: default")
     ap.add_argument("--spmm-sweep", action="store_true",
                     help="instead of the throughput line: HBM and FP64 rates of the product with A "
                          "(hz_apply_A, device blocks) for block widths 1..16 on the bench workload")
@@ -354,6 +356,8 @@ def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, ser
         opts["tensor_cores"] = TENSOR_CORES
     if PERSISTENT >= 0:
         opts["persistent_sweeps"] = PERSISTENT
+    if EMULATE >= 0:
+        opts["emulate_fp64"] = EMULATE
     if MAX_BLOCK > 0:
         opts["max_block"] = MAX_BLOCK
     t0 = time.time()
@@ -394,6 +398,7 @@ def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, ser
            "perturbed_pivots": info["perturbed_pivots"],
            "coarse_fp32": S.options.coarse_fp32, "overlap": S.options.overlap,
            "tensor_cores": S.options.tensor_cores, "persistent_sweeps": S.options.persistent_sweeps,
+           "emulate_fp64": S.options.emulate_fp64 if prec == hz.HZ_PREC_MIXED else 0,
            "max_block": S.options.max_block, "device_gb": S.info()["device_bytes"] / 1e9}
     if with_e2e:
         import numpy as np
@@ -420,6 +425,7 @@ def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, ser
 MAXIT = 500
 TENSOR_CORES = -1
 PERSISTENT = -1
+EMULATE = -1
 MAX_BLOCK = 0
 
 
@@ -589,12 +595,13 @@ def run_scale(args):
 
 
 def main():
-    global MAXIT, TENSOR_CORES, PERSISTENT, MAX_BLOCK
+    global MAXIT, TENSOR_CORES, PERSISTENT, MAX_BLOCK, EMULATE
     args = parse()
     MAX_BLOCK = args.max_block
     MAXIT = args.maxit
     TENSOR_CORES = args.tensor_cores
     PERSISTENT = args.persistent
+    EMULATE = args.emulate_fp64
     if args.impl == "reference":
         run_reference(args)
         return
@@ -692,8 +699,11 @@ def main():
                                 "tflops": q["flops"] / (q["ms"] / 1e3) / 1e12}
     if head == "mixed":
         cf = results[head].get("coarse_fp32", 0)
+        emu = results[head].get("emulate_fp64", 0)
+        c128 = "FP64-class as FP32 pairs" if emu else "c128"
         dtype = ("c64 fine fronts (" + ("3xTF32 tensor cores" if tc_on else "SIMT FP32") + ") + " +
-                 ("c64 coarse level + " if cf else "c128 coarse level + ") + "c128 Krylov/SpMM/outer residual")
+                 ("c64 coarse level + " if cf else "coarse level: c64 fronts, %s E/Krylov + " % c128) +
+                 "%s Krylov/SpMM/outer residual" % c128)
     else:
         dtype = "c128"
     line = {

@@ -546,13 +546,28 @@ void destroy_side(DevMF& mf) {
   mf.ev_fork = mf.ev_join = nullptr;
 }
 
-void upload_split(const CsrC& A, DevSplitCsr& D, DevPool& pool, cudaStream_t st, bool with_f32 = false) {
+// (hi, lo) pairs of FP32 numbers with hi + lo = v to about 48 bits
+static std::vector<float2> df_pairs(const std::vector<double>& v) {
+  std::vector<float2> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) {
+    const float h = (float)v[i];
+    o[i] = make_float2(h, (float)(v[i] - (double)h));
+  }
+  return o;
+}
+
+void upload_split(const CsrC& A, DevSplitCsr& D, DevPool& pool, cudaStream_t st, bool with_f32 = false,
+                  bool with_df = false) {
   CsrR re, im;
   split_re_im(A, re, im);
   if (with_f32) {
     std::vector<float> rf(re.val.begin(), re.val.end()), imf(im.val.begin(), im.val.end());
     D.val_re_f = pool.upload(rf, st);
     D.val_im_f = pool.upload(imf, st);
+  }
+  if (with_df) {
+    D.val_re_df = pool.upload(df_pairs(re.val), st);
+    D.val_im_df = pool.upload(df_pairs(im.val), st);
   }
   D.n = A.nrows;
   D.ncols = A.ncols;
@@ -728,6 +743,8 @@ struct hz_ctx {
   LevelDev lf;                // fine ORAS level
   bool has_coarse = false;
   bool coarse32 = false;      // mixed form with coarse_fp32: the whole of M^{-1} on FP32 blocks
+  bool df = false;            // mixed form with emulate_fp64: products with A and E in double-float
+  float4 *Xdf = nullptr, *XdfH = nullptr;  // double-float copies of the product's input block (fine, coarse)
   Space cspace;
   DevSplitCsr E;
   DevReal Z, ZT;
@@ -772,12 +789,18 @@ struct hz_ctx {
 
 namespace {
 
-void alloc_krylov(DevKrylov& K, int64_t n, int s, int m, DevPool& p, bool fp32) {
+void alloc_krylov(DevKrylov& K, int64_t n, int s, int m, DevPool& p, bool fp32, bool df = false) {
   K.n = n;
   K.s = s;
   K.m = m;
   K.fp32 = fp32 ? 1 : 0;
+  K.df = (df && !fp32) ? 1 : 0;
   K.nblk = 304;
+  if (K.df) {
+    K.Vdf = p.alloc<float4>((size_t)(m + 1) * n * s);
+    K.Wdf = p.alloc<float4>((size_t)n * s);
+    K.hdf = p.alloc<float4>((size_t)(m + 1) * s);
+  }
   const size_t es = fp32 ? sizeof(float2) : sizeof(double2);
   K.V = p.alloc<char>((size_t)(m + 1) * n * s * es);
   K.Zk = p.alloc<char>((size_t)m * n * s * es);
@@ -826,7 +849,13 @@ void ensure_workspace(hz_ctx* c, int s) {
   c->lf.mf.Wout = p.alloc<char>(c->lf.mf.rows_total * s * ef);
   c->lf.mf.P = p.alloc<char>((size_t)std::max(c->lf.mf.max_slots, c->lf.mf.pslots) * MF_TILE_ROWS * s * ef);
   c->lf.mf.s_cap = s;
-  alloc_krylov(c->Kout, n, s, c->opt.restart, p, false);
+  // double-float Arnoldi for the outer space unless block FGMRES or recycling (which read W in FP64)
+  alloc_krylov(c->Kout, n, s, c->opt.restart, p, false,
+               c->df && !c->opt.block_arnoldi && c->opt.recycle == 0);
+  if (c->df) {
+    c->Xdf = p.alloc<float4>(n * s);
+    if (c->has_coarse && !c->coarse32) c->XdfH = p.alloc<float4>(c->cspace.n * s);
+  }
   if (c->opt.recycle > 0) {
     const int rk = c->opt.recycle, m = c->opt.restart;
     c->Kout.Hraw = p.alloc<double2>((size_t)s * (m + 1) * m);
@@ -871,7 +900,7 @@ void ensure_workspace(hz_ctx* c, int s) {
     c->lc.mf.P = p.alloc<char>((size_t)std::max(c->lc.mf.max_slots, c->lc.mf.pslots) * MF_TILE_ROWS * s * ec);
     c->lc.mf.s_cap = s;
     if (c->opt.coarse_mode == HZ_COARSE_GMRES) {
-      alloc_krylov(c->Kin, nh, s, std::max(1, c->opt.coarse_inner_its), p, c->coarse32);
+      alloc_krylov(c->Kin, nh, s, std::max(1, c->opt.coarse_inner_its), p, c->coarse32, c->df);
       CK(cudaMemsetAsync(c->Kin.tol, 0, s * sizeof(double), c->st));
     }
     if (c->coarse32) {
@@ -978,7 +1007,12 @@ void coarse_solve(hz_ctx* c, const double2* rH, double2* yH, int s) {
   krylov_start(K, rH, st);
   for (int j = 0; j < K.m; ++j) {
     apply_oras(L, V + j * vs, Zk + j * vs, nullptr, c->XsubH, s, st);
-    spmm_split(c->E, Zk + j * vs, (double2*)K.W, nullptr, s, 0, st);
+    if (c->df) {
+      to_df(Zk + j * vs, c->XdfH, vs, st);
+      spmm_split_df(c->E, c->XdfH, (double2*)K.W, nullptr, s, 0, st, K.df ? K.Wdf : nullptr);
+    } else {
+      spmm_split(c->E, Zk + j * vs, (double2*)K.W, nullptr, s, 0, st);
+    }
     krylov_arnoldi(K, j, st);
   }
   krylov_update(K, yH, st);
@@ -995,7 +1029,22 @@ void spmm_A(hz_ctx* c, const double2* X, double2* Y, const double2* B, int s, in
   double fl, by;
   spmm_cost(c->A, s, mode == 1, fl, by);
   int id = c->prof.begin(PH_SPMM, c->st);
-  spmm_split(c->A, X, Y, B, s, mode, c->st);
+  if (c->df) {
+    to_df(X, c->Xdf, c->space.n * s, c->st);
+    spmm_split_df(c->A, c->Xdf, Y, B, s, mode, c->st);
+  } else {
+    spmm_split(c->A, X, Y, B, s, mode, c->st);
+  }
+  c->prof.end(id, c->st, fl, by);
+}
+
+// A X into a double-float block (the Krylov product of the double-float Arnoldi)
+void spmm_A_df(hz_ctx* c, const double2* X, float4* Ydf, int s) {
+  double fl, by;
+  spmm_cost(c->A, s, false, fl, by);
+  int id = c->prof.begin(PH_SPMM, c->st);
+  to_df(X, c->Xdf, c->space.n * s, c->st);
+  spmm_split_df(c->A, c->Xdf, nullptr, nullptr, s, 0, c->st, Ydf);
   c->prof.end(id, c->st, fl, by);
 }
 
@@ -1106,7 +1155,10 @@ int fgmres_cycle(hz_ctx* c, int s, int max_its, bool recyc = false) {
   int its = 0;
   for (int j = 0; j < m; ++j) {
     apply_prec(c, (double2*)K.V + j * vs, (double2*)K.Zk + j * vs, s);
-    spmm_A(c, (double2*)K.Zk + j * vs, (double2*)K.W, nullptr, s, 0);
+    if (K.df)
+      spmm_A_df(c, (double2*)K.Zk + j * vs, K.Wdf, s);
+    else
+      spmm_A(c, (double2*)K.Zk + j * vs, (double2*)K.W, nullptr, s, 0);
     int id = c->prof.begin(PH_ARNOLDI, st);
     if (rk > 0) {  // B_j = C^H w, w -= C B_j
       double2* Bj = c->Bc + (size_t)j * rk * s;
@@ -1443,6 +1495,7 @@ int hz_default_options(hz_options* o) {
   o->persistent_sweeps = 0;
   o->factor_fp32 = 1;
   o->recycle = 0;
+  o->emulate_fp64 = 1;
   return HZ_OK;
 }
 
@@ -1500,7 +1553,8 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
     if (c->space.n >= (int64_t)1 << 31) throw HzError{HZ_EINVAL, "more than 2^31 dofs"};
     c->A_host = assemble_global(c->fine, c->space, mvals, omega);
     const bool mixed = o.precision == HZ_PREC_MIXED;
-    upload_split(c->A_host, c->A, c->pool, c->st, mixed);
+    c->df = mixed && o.emulate_fp64 != 0;
+    upload_split(c->A_host, c->A, c->pool, c->st, mixed, c->df);
     std::vector<Subdomain> subs = build_subdomains(c->fine, c->space, part, nparts, mvals, omega, o.overlap);
     const bool tc = mixed && o.tensor_cores != 0;
     const bool pers = o.persistent_sweeps != 0;
@@ -1516,7 +1570,8 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
       // the fine ones; E, Z and the inner coarse GMRES stay FP64 unless coarse_fp32 asks for FP32
       const bool cf32 = mixed && o.coarse_fp32 != 0;
       c->coarse32 = cf32;
-      upload_split(C.E, c->E, c->pool, c->st, cf32 && o.coarse_mode == HZ_COARSE_GMRES);
+      upload_split(C.E, c->E, c->pool, c->st, cf32 && o.coarse_mode == HZ_COARSE_GMRES,
+                   c->df && !cf32 && o.coarse_mode == HZ_COARSE_GMRES);
       upload_real(C.Z, c->Z, c->pool, c->st, cf32);
       upload_real(C.ZT, c->ZT, c->pool, c->st, cf32);
       if (o.coarse_mode == HZ_COARSE_GMRES) {
@@ -2000,12 +2055,14 @@ static double column_bytes(const hz_ctx* c) {
   b += 6.0 * 16.0 * n;                                          // context B, X, R, T, Q, U
   b += ef * ((double)c->lf.sub_rows + (double)c->lf.mf.rows_total + (double)c->lf.mf.max_slots * MF_TILE_ROWS);
   b += 16.0 * n * (2.0 * m + 2.0);                              // V, Zk, W
+  if (c->df) b += 16.0 * n * (m + 3.0);                         // double-float V, W, product input
   if (c->has_coarse) {
     const double nh = (double)c->cspace.n, ec = c->lc.mf.fp32 ? 8.0 : 16.0, ek = c->coarse32 ? 8.0 : 16.0;
     const double mi = std::max(1, c->opt.coarse_inner_its);
     b += 2.0 * 16.0 * nh;                                       // r_H, y_H
     b += ec * ((double)c->lc.sub_rows + (double)c->lc.mf.rows_total + (double)c->lc.mf.max_slots * MF_TILE_ROWS);
     if (c->opt.coarse_mode == HZ_COARSE_GMRES) b += ek * nh * (2.0 * mi + 2.0);
+    if (c->df && !c->coarse32 && c->opt.coarse_mode == HZ_COARSE_GMRES) b += 16.0 * nh * (mi + 3.0);
     if (c->coarse32) b += 8.0 * (2.0 * nh + 3.0 * n);
   }
   return b;

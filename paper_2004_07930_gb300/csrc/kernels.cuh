@@ -25,6 +25,8 @@ struct DevSplitCsr {
   double* val_im = nullptr;
   float* val_re_f = nullptr;  // FP32 copies (mixed-form coarse operator only)
   float* val_im_f = nullptr;
+  float2* val_re_df = nullptr;  // double-float (hi, lo) copies (mixed form, emulated FP64)
+  float2* val_im_df = nullptr;
 };
 
 // Multifrontal factors of a batch of local matrices, grouped by tree height.
@@ -196,7 +198,22 @@ struct DevKrylov {
   int* reorth = nullptr;    // [s] second Gram-Schmidt pass needed
   double2* Hraw = nullptr;  // [s][(m+1) m] unrotated Hessenberg (recycling only; may be NULL)
   int nblk = 0;
+  // double-float Arnoldi (FP64 Krylov spaces of the mixed form, emulate_fp64): the basis is kept in
+  // double-float as well (Vdf, for the Gram-Schmidt products) and A z arrives in Wdf; V stays the
+  // FP64 copy the preconditioner reads
+  int df = 0;
+  float4* Vdf = nullptr;    // [(m+1)][n][s]
+  float4* Wdf = nullptr;    // [n][s]
+  float4* hdf = nullptr;    // [m+1][s] Gram-Schmidt coefficients in double-float
 };
+
+// --- double-float products (mixed form, emulated FP64; df.cu) ---
+// X [count] complex FP64 -> (re_hi, re_lo, im_hi, im_lo)
+void to_df(const double2* X, float4* Y, int64_t count, cudaStream_t st);
+// Y = A X (mode 0) or Y = B - A X (mode 1) with X in double-float, A's double-float values;
+// with Ydf, A X in double-float instead of Y
+void spmm_split_df(const DevSplitCsr& A, const float4* X, double2* Y, const double2* B, int s, int mode,
+                   cudaStream_t st, float4* Ydf = nullptr);
 
 // --- Krylov subspace recycling (option recycle): k vectors U shared by all columns,
 // C = A U orthonormal; blocks [n][k] row-major ---

@@ -28,9 +28,13 @@ def cube():
     return p, T
 
 
-def test_matrix_and_spmm_match_oracle(cube):
+@pytest.mark.parametrize("precision,emulate", [(hz.HZ_PREC_FP64, 1), (hz.HZ_PREC_MIXED, 1), (hz.HZ_PREC_MIXED, 0)])
+def test_matrix_and_spmm_match_oracle(cube, precision, emulate):
+    """Native FP64 product (FP64 form, or mixed with emulate_fp64 = 0) and
+    the double-float product of the mixed form: both within 1e-13 of the
+    largest entry of the SciPy product."""
     p, T = cube
-    with hz.Solver.from_problem(p, coarse_mode=hz.HZ_COARSE_NONE) as S:
+    with hz.Solver.from_problem(p, coarse_mode=hz.HZ_COARSE_NONE, precision=precision, emulate_fp64=emulate) as S:
         perm = dof_perm(S, T.space, 1000.0)
         A = S.matrix_csr()
         Ao = T.A[perm][:, perm]
@@ -38,6 +42,8 @@ def test_matrix_and_spmm_match_oracle(cube):
         X = wl.random_rhs(S.n, 5, 3)
         Y = S.apply_A(X)
         ref = (Ao @ X.T).T
+        print("precision", precision, "emulate_fp64", emulate, "max err / max |ref|",
+              np.abs(Y - ref).max() / np.abs(ref).max())
         assert np.abs(Y - ref).max() <= 1e-13 * np.abs(ref).max()
         info = S.info()
         assert info["n"] == 6859 and info["nnz"] == 299971
