@@ -130,6 +130,7 @@ def parse():
                     help="mixed form: front sweeps on the tcgen05 tensor cores (1) or SIMT (0); -1: library default")
     ap.add_argument("--persistent", type=int, choices=[-1, 0, 1], default=-1,
                     help="SIMT front sweeps as one launch per direction (1) or one per level (0); -1: library default")
+    ap.add_argument("--leaf-size", type=int, default=0, help="nested-dissection leaf size (0: library default)")
     ap.add_argument("--emulate-fp64", type=int, choices=[-1, 0, 1], default=-1,
                     help="mixed form: FP64 products and Arnoldi as FP32 pairs (1) or native FP64 (0); -1: default")
     ap.add_argument("--spmm-sweep", action="store_true",
@@ -358,6 +359,8 @@ def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, ser
         opts["persistent_sweeps"] = PERSISTENT
     if EMULATE >= 0:
         opts["emulate_fp64"] = EMULATE
+    if LEAF > 0:
+        opts["leaf_size"] = LEAF
     if MAX_BLOCK > 0:
         opts["max_block"] = MAX_BLOCK
     t0 = time.time()
@@ -426,6 +429,7 @@ MAXIT = 500
 TENSOR_CORES = -1
 PERSISTENT = -1
 EMULATE = -1
+LEAF = 0
 MAX_BLOCK = 0
 
 
@@ -595,13 +599,14 @@ def run_scale(args):
 
 
 def main():
-    global MAXIT, TENSOR_CORES, PERSISTENT, MAX_BLOCK, EMULATE
+    global MAXIT, TENSOR_CORES, PERSISTENT, MAX_BLOCK, EMULATE, LEAF
     args = parse()
     MAX_BLOCK = args.max_block
     MAXIT = args.maxit
     TENSOR_CORES = args.tensor_cores
     PERSISTENT = args.persistent
     EMULATE = args.emulate_fp64
+    LEAF = args.leaf_size
     if args.impl == "reference":
         run_reference(args)
         return
