@@ -116,11 +116,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the FP64 form")
     ap.add_argument("--fp64-warmup", type=int, default=1, help="warm-up steps of the FP64 form")
-    ap.add_argument("--variants", default="one_level,coarse_fp32,paper_resolution",
+    ap.add_argument("--variants", default="one_level,block,coarse_fp32,paper_resolution",
                     help="extra variants of the headline form: one_level (one-level ORAS; also runs the short "
                          "serving stream), coarse_fp32 (mixed form with the coarse level in complex FP32), "
                          "paper_resolution (two- and one-level at 1.3 Hz on the same mesh: 5 P3 cells per "
-                         "local wavelength as in the paper, coarse mesh at 2.5)")
+                         "local wavelength as in the paper, coarse mesh at 2.5), block (one-level ORAS with "
+                         "block FGMRES, CGS2 + CholQR2, one block of up to 16 sources)")
     ap.add_argument("--maxit", type=int, default=500, help="FGMRES iteration cap (lower it only for profiling runs)")
     ap.add_argument("--max-block", type=int, default=0,
                     help="right-hand sides per block (0: the library default, 64; the 10 Hz workload needs 16 to fit)")
@@ -402,7 +403,7 @@ def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, ser
            "coarse_fp32": S.options.coarse_fp32, "overlap": S.options.overlap,
            "tensor_cores": S.options.tensor_cores, "persistent_sweeps": S.options.persistent_sweeps,
            "emulate_fp64": S.options.emulate_fp64 if prec == hz.HZ_PREC_MIXED else 0,
-           "max_block": S.options.max_block, "device_gb": S.info()["device_bytes"] / 1e9}
+           "max_block": S.options.max_block, "block_arnoldi": S.options.block_arnoldi, "device_gb": S.info()["device_bytes"] / 1e9}
     if with_e2e:
         import numpy as np
 
@@ -660,6 +661,10 @@ def main():
             for nm, c2 in (("two_level", cm), ("one_level", hz.HZ_COARSE_NONE)):
                 variants["paper_resolution_%s_%s" % (nm, forms[0])] = measure_form(
                     p2, forms[0], args.steps, args.warmup, stream, ws, torch, hz, False, coarse_mode=c2)
+        elif v == "block":
+            variants["block_one_level_" + forms[0]] = measure_form(prob, forms[0], args.steps, args.warmup, stream,
+                                                                   ws, torch, hz, False, coarse_mode=hz.HZ_COARSE_NONE,
+                                                                   block_arnoldi=1, max_block=16)
         elif v == "coarse_fp32" and forms[0] == "mixed" and args.coarse != "none":
             variants["coarse_fp32_mixed"] = measure_form(prob, "mixed", args.steps, args.warmup, stream, ws, torch,
                                                          hz, False, coarse_mode=cm, coarse_fp32=1)

@@ -79,6 +79,32 @@ __global__ void k_spmm_df(int64_t n, int s, const int64_t* __restrict__ rp_re, c
   }
 }
 
+// Y = R X for a real CSR R (the coarse restriction Z^T and prolongation Z),
+// X in double-float, Y in FP64
+__global__ void k_spmm_real_df(int64_t n, int s, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                               const float2* __restrict__ val, const float4* __restrict__ X, double2* __restrict__ Y) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t r = g / s;
+  const int c = (int)(g - r * s);
+  if (r >= n) return;
+  float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+#pragma unroll 4
+  for (int64_t p = rp[r], pe = rp[r + 1]; p < pe; ++p) {
+    const float2 a = val[p];
+    const float4 x = X[(int64_t)col[p] * s + c];
+    df_mac(rh, rl, a.x, a.y, x.x, x.y);
+    df_mac(ih, il, a.x, a.y, x.z, x.w);
+  }
+  Y[g] = make_double2(f2d(rh) + f2d(rl), f2d(ih) + f2d(il));
+}
+
+void spmm_real_df(int64_t nrows, const int64_t* rp, const int32_t* col, const float2* val, const float4* X,
+                  double2* Y, int s, cudaStream_t st) {
+  const int64_t work = nrows * s;
+  if (work == 0) return;
+  { k_spmm_real_df<<<grid_for(work, 256), 256, 0, st>>>(nrows, s, rp, col, val, X, Y); count_launch(); }
+}
+
 void to_df(const double2* X, float4* Y, int64_t count, cudaStream_t st) {
   if (count) { k_to_df<<<grid_for(count, 256), 256, 0, st>>>(X, Y, count); count_launch(); }
 }

@@ -104,6 +104,8 @@ struct MFHost {
 // sub_off[i] is the first row of subdomain i in the flat sub-vector.
 constexpr int MF_TILE_ROWS = 128;  // output rows per sweep tile (MF_TILE in mf.cu)
 constexpr int MF_TILE_K = 128;     // reduction length per sweep tile (MF_TK in mf.cu)
+constexpr int MF_TILE_K_ONE = 256; // a row block with at most this many reduction indices is one tile
+                                   // (staged MF_TILE_K at a time), without partials or a reduce
 
 void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const FrontTree*>& trees,
               const std::vector<int64_t>& sub_off, bool fp32, bool fr32, bool tc, bool persistent, DevMF& mf,
@@ -273,6 +275,8 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
       (fwd ? fs : bsl).push_back(tile);
     }
   };
+  // single-tile limit: the tensor-core tiles cover at most MF_TILE_K reduction indices
+  const int kone = tc ? MF_TILE_K : MF_TILE_K_ONE;
   info.fwd_cmacs.assign(maxh + 1, 0.0);
   info.bwd_cmacs.assign(maxh + 1, 0.0);
   int64_t max_slots = 1;
@@ -287,7 +291,7 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
       for (int r0 = 0; r0 < f[g]; r0 += MF_TILE_ROWS) {
         const int kend = r0 < k[g] ? std::min(k[g], r0 + MF_TILE_ROWS) : k[g];
         const int nk = (kend + MF_TILE_K - 1) / MF_TILE_K;
-        if (nk <= 1) {
+        if (nk <= 1 || kend <= kone) {
           ftiles.push_back(make_int4(g, r0, 0, -1));
           classify(true, ftiles.back());
           continue;
@@ -300,7 +304,7 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
       }
       for (int j0 = 0; j0 < k[g]; j0 += MF_TILE_ROWS) {
         const int nk = (f[g] - j0 + MF_TILE_K - 1) / MF_TILE_K;
-        if (nk == 1) {
+        if (nk == 1 || f[g] - j0 <= kone) {
           btiles.push_back(make_int4(g, j0, j0, -1));
           classify(false, btiles.back());
           continue;
@@ -586,9 +590,11 @@ struct DevReal {
   int64_t* rp = nullptr;
   int32_t* col = nullptr;
   double* val = nullptr;
-  float* val_f = nullptr;  // FP32 copy (mixed form)
+  float* val_f = nullptr;    // FP32 copy (mixed form)
+  float2* val_df = nullptr;  // double-float copy (mixed form, emulate_fp64)
 };
-void upload_real(const CsrR& A, DevReal& D, DevPool& pool, cudaStream_t st, bool with_f32 = false) {
+void upload_real(const CsrR& A, DevReal& D, DevPool& pool, cudaStream_t st, bool with_f32 = false,
+                 bool with_df = false) {
   D.n = A.nrows;
   D.nnz = (int64_t)A.col.size();
   D.rp = pool.upload(A.rowptr, st);
@@ -598,6 +604,7 @@ void upload_real(const CsrR& A, DevReal& D, DevPool& pool, cudaStream_t st, bool
     std::vector<float> vf(A.val.begin(), A.val.end());
     D.val_f = pool.upload(vf, st);
   }
+  if (with_df) D.val_df = pool.upload(df_pairs(A.val), st);
 }
 
 struct LevelDev {             // one level of ORAS on the device
@@ -797,7 +804,6 @@ void alloc_krylov(DevKrylov& K, int64_t n, int s, int m, DevPool& p, bool fp32, 
   K.df = (df && !fp32) ? 1 : 0;
   K.nblk = 304;
   if (K.df) {
-    K.Vdf = p.alloc<float4>((size_t)(m + 1) * n * s);
     K.Wdf = p.alloc<float4>((size_t)n * s);
     K.hdf = p.alloc<float4>((size_t)(m + 1) * s);
   }
@@ -1124,10 +1130,20 @@ void apply_prec(hz_ctx* c, const double2* V, double2* Zout, int s) {
     return;
   }
   int id = c->prof.begin(PH_COARSE, st);
-  spmm_real(c->ZT.n, c->ZT.rp, c->ZT.col, c->ZT.val, V, c->rH, s, st);   // r_H = Z^T v
+  if (c->ZT.val_df) {  // double-float restriction and prolongation
+    to_df(V, c->Xdf, c->space.n * s, st);
+    spmm_real_df(c->ZT.n, c->ZT.rp, c->ZT.col, c->ZT.val_df, c->Xdf, c->rH, s, st);   // r_H = Z^T v
+  } else {
+    spmm_real(c->ZT.n, c->ZT.rp, c->ZT.col, c->ZT.val, V, c->rH, s, st);
+  }
   run_graph(c->opt.use_graphs ? &c->g_coarse : nullptr, s, st,
             [&]() { coarse_solve(c, c->rH, c->yH, s); });                 // y_H ~ E^{-1} r_H
-  spmm_real(c->Z.n, c->Z.rp, c->Z.col, c->Z.val, c->yH, c->Q, s, st);    // q = Z y_H
+  if (c->Z.val_df) {
+    to_df(c->yH, c->XdfH, c->cspace.n * s, st);
+    spmm_real_df(c->Z.n, c->Z.rp, c->Z.col, c->Z.val_df, c->XdfH, c->Q, s, st);       // q = Z y_H
+  } else {
+    spmm_real(c->Z.n, c->Z.rp, c->Z.col, c->Z.val, c->yH, c->Q, s, st);
+  }
   if (id >= 0) {
     double cf, cb;
     coarse_cost(c, s, false, cf, cb);
@@ -1572,8 +1588,8 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
       c->coarse32 = cf32;
       upload_split(C.E, c->E, c->pool, c->st, cf32 && o.coarse_mode == HZ_COARSE_GMRES,
                    c->df && !cf32 && o.coarse_mode == HZ_COARSE_GMRES);
-      upload_real(C.Z, c->Z, c->pool, c->st, cf32);
-      upload_real(C.ZT, c->ZT, c->pool, c->st, cf32);
+      upload_real(C.Z, c->Z, c->pool, c->st, cf32, c->df && !cf32);
+      upload_real(C.ZT, c->ZT, c->pool, c->st, cf32, c->df && !cf32);
       if (o.coarse_mode == HZ_COARSE_GMRES) {
         std::vector<Subdomain> csubs =
             build_subdomains(c->coarse, c->cspace, C.part, nparts, C.mvals, omega, o.overlap);
@@ -2055,14 +2071,14 @@ static double column_bytes(const hz_ctx* c) {
   b += 6.0 * 16.0 * n;                                          // context B, X, R, T, Q, U
   b += ef * ((double)c->lf.sub_rows + (double)c->lf.mf.rows_total + (double)c->lf.mf.max_slots * MF_TILE_ROWS);
   b += 16.0 * n * (2.0 * m + 2.0);                              // V, Zk, W
-  if (c->df) b += 16.0 * n * (m + 3.0);                         // double-float V, W, product input
+  if (c->df) b += 16.0 * n * 2.0;                               // double-float W and product input
   if (c->has_coarse) {
     const double nh = (double)c->cspace.n, ec = c->lc.mf.fp32 ? 8.0 : 16.0, ek = c->coarse32 ? 8.0 : 16.0;
     const double mi = std::max(1, c->opt.coarse_inner_its);
     b += 2.0 * 16.0 * nh;                                       // r_H, y_H
     b += ec * ((double)c->lc.sub_rows + (double)c->lc.mf.rows_total + (double)c->lc.mf.max_slots * MF_TILE_ROWS);
     if (c->opt.coarse_mode == HZ_COARSE_GMRES) b += ek * nh * (2.0 * mi + 2.0);
-    if (c->df && !c->coarse32 && c->opt.coarse_mode == HZ_COARSE_GMRES) b += 16.0 * nh * (mi + 3.0);
+    if (c->df && !c->coarse32 && c->opt.coarse_mode == HZ_COARSE_GMRES) b += 16.0 * nh * 2.0;
     if (c->coarse32) b += 8.0 * (2.0 * nh + 3.0 * n);
   }
   return b;

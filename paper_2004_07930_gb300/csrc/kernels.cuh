@@ -198,11 +198,9 @@ struct DevKrylov {
   int* reorth = nullptr;    // [s] second Gram-Schmidt pass needed
   double2* Hraw = nullptr;  // [s][(m+1) m] unrotated Hessenberg (recycling only; may be NULL)
   int nblk = 0;
-  // double-float Arnoldi (FP64 Krylov spaces of the mixed form, emulate_fp64): the basis is kept in
-  // double-float as well (Vdf, for the Gram-Schmidt products) and A z arrives in Wdf; V stays the
-  // FP64 copy the preconditioner reads
+  // double-float Arnoldi (FP64 Krylov spaces of the mixed form, emulate_fp64): A z arrives in
+  // double-float (Wdf); the basis V stays FP64 and is split into FP32 pairs as it is read
   int df = 0;
-  float4* Vdf = nullptr;    // [(m+1)][n][s]
   float4* Wdf = nullptr;    // [n][s]
   float4* hdf = nullptr;    // [m+1][s] Gram-Schmidt coefficients in double-float
 };
@@ -214,6 +212,10 @@ void to_df(const double2* X, float4* Y, int64_t count, cudaStream_t st);
 // with Ydf, A X in double-float instead of Y
 void spmm_split_df(const DevSplitCsr& A, const float4* X, double2* Y, const double2* B, int s, int mode,
                    cudaStream_t st, float4* Ydf = nullptr);
+
+// Y = R X for a real CSR R with double-float values, X in double-float, Y in FP64
+void spmm_real_df(int64_t nrows, const int64_t* rp, const int32_t* col, const float2* val, const float4* X,
+                  double2* Y, int s, cudaStream_t st);
 
 // --- Krylov subspace recycling (option recycle): k vectors U shared by all columns,
 // C = A U orthonormal; blocks [n][k] row-major ---

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "df.cuh"
 #include "kernels.cuh"
@@ -302,10 +303,18 @@ static void krylov_arnoldi_t(DevKrylov& K, int j, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // Double-float Arnoldi (FP64 Krylov spaces of the mixed form with
 // emulate_fp64): the same CGS with selective reorthogonalisation, the
-// products and updates on double-float blocks (FP32 pairs), the partial dot
-// products of each thread converted to FP64 and summed in FP64 in the same
-// fixed order as above; Hessenberg, rotations and least squares unchanged.
+// products and updates in double-float arithmetic (FP32 pairs). The basis
+// stays in FP64 (the preconditioner reads it) and is split into FP32 pairs by
+// its bit layout as it is read, so that it costs no second copy; W (A z) is a
+// double-float block. The partial dot products of each thread are converted
+// to FP64 and summed in FP64 in the same fixed order as above; Hessenberg,
+// rotations and least squares unchanged.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 df_split2(const double2 v) {
+  const float2 r = df_split(v.x), i = df_split(v.y);
+  return make_float4(r.x, r.y, i.x, i.y);
+}
+
 // (reh, rel, imh, iml) += conj(v) w
 __device__ __forceinline__ void df_conj_mac(float4& a, const float4 v, const float4 w) {
   df_mac(a.x, a.y, v.x, v.y, w.x, w.y);    // re += vr wr
@@ -314,7 +323,8 @@ __device__ __forceinline__ void df_conj_mac(float4& a, const float4 v, const flo
   df_mac(a.z, a.w, -v.z, -v.w, w.x, w.y);  // im -= vi wr
 }
 
-__global__ void k_mdot_df(const float4* __restrict__ Vb, int64_t vstride, int i0, int ni,
+template <typename VB>  // basis: double2 (FP64, split as read) or float4 (double-float)
+__global__ void k_mdot_df(const VB* __restrict__ Vb, int64_t vstride, int i0, int ni,
                           const float4* __restrict__ W, int64_t n, int s, int64_t rows_per_blk,
                           double2* __restrict__ part, int mstride, const int* __restrict__ mask) {
   __shared__ double2 sh[KBLOCK];
@@ -329,7 +339,13 @@ __global__ void k_mdot_df(const float4* __restrict__ Vb, int64_t vstride, int i0
     const float4 w = W[r * s + c];
 #pragma unroll
     for (int q = 0; q < IG; ++q)
-      if (q < ni) df_conj_mac(acc[q], Vb[(int64_t)(i0 + q) * vstride + r * s + c], w);
+      if (q < ni) {
+        const VB vb = Vb[(int64_t)(i0 + q) * vstride + r * s + c];
+        if constexpr (std::is_same<VB, float4>::value)
+          df_conj_mac(acc[q], vb, w);
+        else
+          df_conj_mac(acc[q], df_split2(vb), w);
+      }
   }
   for (int q = 0; q < ni; ++q) {
     sh[threadIdx.x] = make_double2(f2d(acc[q].x) + f2d(acc[q].y), f2d(acc[q].z) + f2d(acc[q].w));
@@ -343,14 +359,15 @@ __global__ void k_mdot_df(const float4* __restrict__ Vb, int64_t vstride, int i0
   }
 }
 
-static void mdot_df(DevKrylov& K, const float4* Vb, int64_t vstride, int ni, const float4* W, double2* out,
+template <typename VB>
+static void mdot_df(DevKrylov& K, const VB* Vb, int64_t vstride, int ni, const float4* W, double2* out,
                     cudaStream_t st, const int* mask = nullptr) {
   const int s = K.s;
   const int block = (KBLOCK / s) * s;
   const int64_t rpb = (K.n + K.nblk - 1) / K.nblk;
   for (int i0 = 0; i0 < ni; i0 += IG)
-    { k_mdot_df<<<K.nblk, block, 0, st>>>(Vb, vstride, i0, std::min(IG, ni - i0), W, K.n, s, rpb, K.hpart, K.m + 1,
-                                        mask); count_launch(); }
+    { k_mdot_df<VB><<<K.nblk, block, 0, st>>>(Vb, vstride, i0, std::min(IG, ni - i0), W, K.n, s, rpb, K.hpart,
+                                            K.m + 1, mask); count_launch(); }
   { k_reduce_part<<<grid_for((int64_t)ni * s * 32, 256), 256, 0, st>>>(K.hpart, K.nblk, ni, s, K.m + 1, out); count_launch(); }
 }
 
@@ -362,8 +379,8 @@ __global__ void k_h_df(const double2* __restrict__ h, float4* __restrict__ out, 
   out[g] = make_float4(a.x, a.y, b.x, b.y);
 }
 
-// W[r][c] -= sum_{i<ni} V_i[r][c] h[i][c], double-float
-__global__ void k_update_df(const float4* __restrict__ Vb, int64_t vstride, int ni, const float4* __restrict__ h,
+// W[r][c] -= sum_{i<ni} V_i[r][c] h[i][c], double-float (V in FP64, split as read)
+__global__ void k_update_df(const double2* __restrict__ Vb, int64_t vstride, int ni, const float4* __restrict__ h,
                             float4* __restrict__ W, int64_t n, int s, const int* __restrict__ mask) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n * s) return;
@@ -371,7 +388,7 @@ __global__ void k_update_df(const float4* __restrict__ Vb, int64_t vstride, int 
   if (mask && !mask[c]) return;
   float4 w = W[g];
   for (int i = 0; i < ni; ++i) {
-    const float4 v = Vb[i * vstride + g], hc = h[i * s + c];
+    const float4 v = df_split2(Vb[i * vstride + g]), hc = h[i * s + c];
     df_mac(w.x, w.y, -v.x, -v.y, hc.x, hc.y);  // re -= vr hr
     df_mac(w.x, w.y, v.z, v.w, hc.z, hc.w);    // re += vi hi
     df_mac(w.z, w.w, -v.x, -v.y, hc.z, hc.w);  // im -= vr hi
@@ -382,9 +399,9 @@ __global__ void k_update_df(const float4* __restrict__ Vb, int64_t vstride, int 
   W[g] = w;
 }
 
-// v = w beta[c]: the double-float basis vector and its FP64 copy
-__global__ void k_scale_df(const float4* __restrict__ X, const double* __restrict__ beta, float4* __restrict__ Ydf,
-                           double2* __restrict__ Y, int64_t n, int s) {
+// v = w beta[c] (double-float product, stored in FP64: hi + lo is exact in FP64)
+__global__ void k_scale_df(const float4* __restrict__ X, const double* __restrict__ beta, double2* __restrict__ Y,
+                           int64_t n, int s) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n * s) return;
   const float2 b = df_split(beta[g % s]);
@@ -392,7 +409,6 @@ __global__ void k_scale_df(const float4* __restrict__ X, const double* __restric
   float4 y;
   df_mul(y.x, y.y, x.x, x.y, b.x, b.y);
   df_mul(y.z, y.w, x.z, x.w, b.x, b.y);
-  Ydf[g] = y;
   Y[g] = make_double2(f2d(y.x) + f2d(y.y), f2d(y.z) + f2d(y.w));
 }
 
@@ -402,17 +418,18 @@ static void krylov_arnoldi_df(DevKrylov& K, int j, cudaStream_t st) {
   double2* nrm = K.h2 + (int64_t)K.m * K.s;
   const int nh = (j + 1) * K.s;
   mdot_df(K, K.Wdf, 0, 1, K.Wdf, nrm, st);
-  mdot_df(K, K.Vdf, vs, j + 1, K.Wdf, K.h1, st);
+  const double2* Vb = (const double2*)K.V;
+  mdot_df(K, Vb, vs, j + 1, K.Wdf, K.h1, st);
   { k_h_df<<<grid_for(nh, 128), 128, 0, st>>>(K.h1, K.hdf, nh); count_launch(); }
-  { k_update_df<<<gr, 256, 0, st>>>(K.Vdf, vs, j + 1, K.hdf, K.Wdf, K.n, K.s, nullptr); count_launch(); }
+  { k_update_df<<<gr, 256, 0, st>>>(Vb, vs, j + 1, K.hdf, K.Wdf, K.n, K.s, nullptr); count_launch(); }
   { k_reorth_flags<<<1, 64, 0, st>>>(K.s, j, K.h1, nrm, K.reorth); count_launch(); }
-  mdot_df(K, K.Vdf, vs, j + 1, K.Wdf, K.h2, st, K.reorth);
+  mdot_df(K, Vb, vs, j + 1, K.Wdf, K.h2, st, K.reorth);
   { k_h_df<<<grid_for(nh, 128), 128, 0, st>>>(K.h2, K.hdf, nh); count_launch(); }
-  { k_update_df<<<gr, 256, 0, st>>>(K.Vdf, vs, j + 1, K.hdf, K.Wdf, K.n, K.s, K.reorth); count_launch(); }
+  { k_update_df<<<gr, 256, 0, st>>>(Vb, vs, j + 1, K.hdf, K.Wdf, K.n, K.s, K.reorth); count_launch(); }
   mdot_df(K, K.Wdf, 0, 1, K.Wdf, nrm, st);
   { k_arnoldi_finish<<<1, 64, 0, st>>>(K.s, K.m, j, K.h1, K.h2, nrm, K.H, K.cs, K.sn, K.g, K.beta, K.tol, K.kc, K.done,
                                      K.res, K.Hraw); count_launch(); }
-  { k_scale_df<<<gr, 256, 0, st>>>(K.Wdf, K.beta, K.Vdf + (j + 1) * vs, (double2*)K.V + (j + 1) * vs, K.n, K.s); count_launch(); }
+  { k_scale_df<<<gr, 256, 0, st>>>(K.Wdf, K.beta, (double2*)K.V + (j + 1) * vs, K.n, K.s); count_launch(); }
 }
 
 template <typename V>
@@ -432,7 +449,6 @@ void krylov_start(DevKrylov& K, const void* R, cudaStream_t st) {
     krylov_start_t<float2>(K, (const float2*)R, st);
   } else {
     krylov_start_t<double2>(K, (const double2*)R, st);
-    if (K.df) to_df((const double2*)K.V, K.Vdf, K.n * K.s, st);
   }
 }
 void krylov_arnoldi(DevKrylov& K, int j, cudaStream_t st) {
