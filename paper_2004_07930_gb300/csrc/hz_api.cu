@@ -104,8 +104,6 @@ struct MFHost {
 // sub_off[i] is the first row of subdomain i in the flat sub-vector.
 constexpr int MF_TILE_ROWS = 128;  // output rows per sweep tile (MF_TILE in mf.cu)
 constexpr int MF_TILE_K = 128;     // reduction length per sweep tile (MF_TK in mf.cu)
-constexpr int MF_TILE_K_ONE = 256; // a row block with at most this many reduction indices is one tile
-                                   // (staged MF_TILE_K at a time), without partials or a reduce
 
 void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const FrontTree*>& trees,
               const std::vector<int64_t>& sub_off, bool fp32, bool fr32, bool tc, bool persistent, DevMF& mf,
@@ -275,8 +273,6 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
       (fwd ? fs : bsl).push_back(tile);
     }
   };
-  // single-tile limit: the tensor-core tiles cover at most MF_TILE_K reduction indices
-  const int kone = tc ? MF_TILE_K : MF_TILE_K_ONE;
   info.fwd_cmacs.assign(maxh + 1, 0.0);
   info.bwd_cmacs.assign(maxh + 1, 0.0);
   int64_t max_slots = 1;
@@ -291,7 +287,7 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
       for (int r0 = 0; r0 < f[g]; r0 += MF_TILE_ROWS) {
         const int kend = r0 < k[g] ? std::min(k[g], r0 + MF_TILE_ROWS) : k[g];
         const int nk = (kend + MF_TILE_K - 1) / MF_TILE_K;
-        if (nk <= 1 || kend <= kone) {
+        if (nk <= 1) {
           ftiles.push_back(make_int4(g, r0, 0, -1));
           classify(true, ftiles.back());
           continue;
@@ -304,7 +300,7 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
       }
       for (int j0 = 0; j0 < k[g]; j0 += MF_TILE_ROWS) {
         const int nk = (f[g] - j0 + MF_TILE_K - 1) / MF_TILE_K;
-        if (nk == 1 || f[g] - j0 <= kone) {
+        if (nk == 1) {
           btiles.push_back(make_int4(g, j0, j0, -1));
           classify(false, btiles.back());
           continue;
@@ -446,6 +442,7 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
   mf.amap_pos = pool.upload(amap_pos, st);
   mf.amap_val = pool.upload(amap_val, st);
   mf.Aval = pool.upload(Aval, st);
+  mf.aval_n = (int64_t)Aval.size();
   mf.fr32 = fr32 ? 1 : 0;
   mf.F = fr32 ? (void*)pool.alloc<float2>(Foff[nf]) : (void*)pool.alloc<double2>(Foff[nf]);
   {
@@ -558,6 +555,13 @@ static std::vector<float2> df_pairs(const std::vector<double>& v) {
     o[i] = make_float2(h, (float)(v[i] - (double)h));
   }
   return o;
+}
+
+void upload_split_df(const CsrC& A, DevSplitCsr& D, DevPool& pool, cudaStream_t st) {
+  CsrR re, im;
+  split_re_im(A, re, im);
+  D.val_re_df = pool.upload(df_pairs(re.val), st);
+  D.val_im_df = pool.upload(df_pairs(im.val), st);
 }
 
 void upload_split(const CsrC& A, DevSplitCsr& D, DevPool& pool, cudaStream_t st, bool with_f32 = false,
@@ -1570,7 +1574,7 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
     c->A_host = assemble_global(c->fine, c->space, mvals, omega);
     const bool mixed = o.precision == HZ_PREC_MIXED;
     c->df = mixed && o.emulate_fp64 != 0;
-    upload_split(c->A_host, c->A, c->pool, c->st, mixed, c->df);
+    upload_split(c->A_host, c->A, c->pool, c->st, mixed);
     std::vector<Subdomain> subs = build_subdomains(c->fine, c->space, part, nparts, mvals, omega, o.overlap);
     const bool tc = mixed && o.tensor_cores != 0;
     const bool pers = o.persistent_sweeps != 0;
@@ -1620,6 +1624,20 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
       c->pool.free_one(c->lc.mf.F, c->lc.mf.F_total * (c->lc.mf.fr32 ? sizeof(float2) : sizeof(double2)));
       c->lc.mf.F = nullptr;
     }
+    // the assembly maps and local matrix values are only read by the factorisation
+    for (DevMF* mf : {&c->lf.mf, &c->lc.mf}) {
+      if (!mf->amap_ptr) continue;
+      c->pool.free_one(mf->amap_ptr, (mf->nfronts + 1) * sizeof(int64_t));
+      c->pool.free_one(mf->amap_pos, std::max<int64_t>(1, mf->amap_total) * sizeof(int));
+      c->pool.free_one(mf->amap_val, std::max<int64_t>(1, mf->amap_total) * sizeof(int64_t));
+      c->pool.free_one(mf->Aval, std::max<int64_t>(1, mf->aval_n) * sizeof(double2));
+      mf->amap_ptr = nullptr;
+      mf->amap_pos = nullptr;
+      mf->amap_val = nullptr;
+      mf->Aval = nullptr;
+    }
+    // double-float values of A (mixed form, emulate_fp64), once the factorisation workspaces are gone
+    if (c->df) upload_split_df(c->A_host, c->A, c->pool, c->st);
     c->perturbed = pf + pcnt;
     if (o.pivot_tau == 0.0 && c->perturbed) throw HzError{HZ_ESINGULAR, "zero pivot in a local factorisation"};
     if (o.debug_bounds) {

@@ -69,7 +69,8 @@ struct DevMF {
   int64_t* amap_ptr = nullptr;  // [nfronts+1]
   int* amap_pos = nullptr;      // front position r + c f of each assembled entry
   int64_t* amap_val = nullptr;  // index into Aval
-  double2* Aval = nullptr;      // concatenated local matrix values
+  double2* Aval = nullptr;      // concatenated local matrix values (freed after the factorisation)
+  int64_t aval_n = 0;
   void* F = nullptr;            // factorisation workspace, double2 or float2 (fr32), freed after setup
   int fr32 = 0;                 // factorisation in complex FP32 (mixed form, fine level)
   float factor_ms = 0.f, inverse_ms = 0.f;  // device time of the assembly + LDL^T and of the partitioned inverse

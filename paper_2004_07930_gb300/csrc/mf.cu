@@ -132,8 +132,7 @@ __device__ __forceinline__ V ldv(const V* p) {
 // staging and the small shared-memory footprint leaves room for several CTAs
 // per SM. A tile with
 // slot >= 0 writes its partial result to P; the others apply the epilogue.
-constexpr int MF_UNROLL = 4;
-static_assert(MF_TK % MF_UNROLL == 0, "a batch of factor columns never straddles two staged chunks");
+constexpr int MF_UNROLL = 8;
 template <typename V, int S, bool FWD, bool CG>
 __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restrict__ kk, const int* __restrict__ ff,
                                            const int64_t* __restrict__ rowoff, const int64_t* __restrict__ Moff,
@@ -148,9 +147,7 @@ __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restric
   const int ld = FWD ? f : k;
   const int kend = FWD ? ((r0 < k) ? min(k, r0 + MF_TILE) : k) : f;
   const int kbeg = FWD ? c0 : max(c0, r0);  // X_t^T is zero left of the diagonal of its pivot block
-  // a split tile covers MF_TK reduction indices; a row block's only tile covers all of them
-  // (at most MF_TK_ONE, planned on the host), staged MF_TK at a time
-  const int kstop = slot < 0 ? kend : min(kend, c0 + MF_TK);
+  const int kstop = min(kend, c0 + MF_TK);
   const V* Mt = M + Moff[t];
   const int64_t ro = rowoff[t];
   const int tid = threadIdx.x;
@@ -163,60 +160,47 @@ __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restric
 #pragma unroll
   for (int u = 0; u < MF_UNROLL; ++u)
     m0[u] = (act && u < lmax) ? __ldg(mcol + (int64_t)u * ld) : mk2((decltype(V::x))0, (decltype(V::x))0);
-  // stage the input rows of reduction indices [l0, l0 + MF_TK) of the tile
-  auto stage = [&](int l0) {
-    const int lc = min(MF_TK, lmax - l0);
-    for (int l = tid; l < lc; l += MF_TILE) {
-      const int64_t R = ro + kbeg + l0 + l;
-      const int local = kbeg + l0 + l;
-      V v[S];
-      const V* src = (FWD || local >= k) ? Xsub + (int64_t)rows[R] * s : Wout + R * s;
+  for (int l = tid; l < lmax; l += MF_TILE) {
+    const int64_t R = ro + kbeg + l;
+    const int local = kbeg + l;
+    V v[S];
+    const V* src = (FWD || local >= k) ? Xsub + (int64_t)rows[R] * s : Wout + R * s;
 #pragma unroll
-      for (int c = 0; c < S; ++c) v[c] = c < s ? ldv<CG>(src + c) : mk2((decltype(V::x))0, (decltype(V::x))0);
-      if (FWD) {
-        const int64_t pe = cptr[R + 1];
-        for (int64_t p = cptr[R]; p < pe; ++p) {
-          const V* w = Wout + (int64_t)cidx[p] * s;
+    for (int c = 0; c < S; ++c) v[c] = c < s ? ldv<CG>(src + c) : mk2((decltype(V::x))0, (decltype(V::x))0);
+    if (FWD) {
+      const int64_t pe = cptr[R + 1];
+      for (int64_t p = cptr[R]; p < pe; ++p) {
+        const V* w = Wout + (int64_t)cidx[p] * s;
 #pragma unroll
-          for (int c = 0; c < S; ++c)
-            if (c < s) v[c] = c_add(v[c], ldv<CG>(w + c));
-        }
+        for (int c = 0; c < S; ++c)
+          if (c < s) v[c] = c_add(v[c], ldv<CG>(w + c));
       }
-#pragma unroll
-      for (int c = 0; c < S; ++c) bs[l][c] = v[c];
     }
-  };
-  stage(0);
+#pragma unroll
+    for (int c = 0; c < S; ++c) bs[l][c] = v[c];
+  }
   __syncthreads();
   V acc[S];
 #pragma unroll
   for (int c = 0; c < S; ++c) acc[c] = mk2((decltype(V::x))0, (decltype(V::x))0);
-  // software pipeline: the next MF_UNROLL factor columns are in flight while the current ones
-  // are used; every MF_TK indices the next chunk of input rows is staged (the loop bounds are
-  // the same for all threads of the tile, so the barriers are uniform)
-  int j = 0;
-  while (j < lmax) {
-    const int jn = j + MF_UNROLL;
-    V m1[MF_UNROLL];
+  if (act) {
+    // software pipeline: the next MF_UNROLL factor columns are in flight while the current ones are used
+    int j = 0;
+    while (j < lmax) {
+      const int jn = j + MF_UNROLL;
+      V m1[MF_UNROLL];
 #pragma unroll
-    for (int u = 0; u < MF_UNROLL; ++u)
-      m1[u] = (act && jn + u < lmax) ? __ldg(mcol + (int64_t)(jn + u) * ld) : mk2((decltype(V::x))0, (decltype(V::x))0);
-    if (act) {
-      const int jb = j % MF_TK;
+      for (int u = 0; u < MF_UNROLL; ++u)
+        m1[u] = jn + u < lmax ? __ldg(mcol + (int64_t)(jn + u) * ld) : mk2((decltype(V::x))0, (decltype(V::x))0);
 #pragma unroll
       for (int u = 0; u < MF_UNROLL; ++u)
         if (j + u < lmax)
 #pragma unroll
-          for (int c = 0; c < S; ++c) acc[c] = c_fma(m0[u], bs[jb + u][c], acc[c]);
-    }
+          for (int c = 0; c < S; ++c) acc[c] = c_fma(m0[u], bs[j + u][c], acc[c]);
 #pragma unroll
-    for (int u = 0; u < MF_UNROLL; ++u) m0[u] = m1[u];
-    if (jn < lmax && jn % MF_TK == 0) {
-      __syncthreads();
-      stage(jn);
-      __syncthreads();
+      for (int u = 0; u < MF_UNROLL; ++u) m0[u] = m1[u];
+      j = jn;
     }
-    j = jn;
   }
   if (slot >= 0) {
     V* out = P + ((int64_t)slot * MF_TILE + tid) * s;
