@@ -122,24 +122,40 @@ __device__ __forceinline__ V ldv(const V* p) {
     return *p;
 }
 
-// One tile. Each thread owns one output row (MF_TILE threads) and keeps the s
-// right-hand sides as register accumulators. The tile's input rows are
-// staged once in shared memory (read as broadcasts); each thread streams its
-// row of the factor tile straight from global memory (a warp reads 32
-// consecutive entries of one factor column per load), the next MF_UNROLL
-// columns in flight while the current ones are used (the first batch while
-// the input rows are staged), so the only barrier is the one after the
-// staging and the small shared-memory footprint leaves room for several CTAs
-// per SM. A tile with
-// slot >= 0 writes its partial result to P; the others apply the epilogue.
+// One tile. TPR threads share each output row (MF_TILE x TPR threads), each
+// keeping S/TPR of the right-hand sides as register accumulators, so that a
+// tile's serial work per thread (and its latency) shrinks with TPR while the
+// accumulation order of every column stays the same. The tile's input rows
+// are staged once in shared memory (read as broadcasts); each thread streams
+// its row of the factor tile straight from global memory (the TPR threads of
+// a row read the same entry, a warp 32/TPR consecutive entries of one factor
+// column per load), the next MF_UNROLL columns in flight while the current
+// ones are used (the first batch while the input rows are staged), so the only
+// barrier is the one after the staging and the small shared-memory footprint
+// leaves room for several CTAs per SM. A tile with slot >= 0 writes its
+// partial result to P; the others apply the epilogue.
 constexpr int MF_UNROLL = 8;
-template <typename V, int S, bool FWD, bool CG>
+// threads per output row for a block width S (the per-level launches); the
+// persistent sweep keeps one thread per row
+template <int S>
+__host__ __device__ constexpr int tile_tpr() {
+  return S >= 16 ? 4 : (S >= 8 ? 2 : 1);
+}
+// complex FP32 tiles of up to 16 columns: at least 1024 resident threads per SM
+// (64 registers per thread; wider blocks keep their accumulators unbounded)
+template <typename V, int S>
+__host__ __device__ constexpr int tile_min_blocks() {
+  return (sizeof(V) == 8 && S <= 16) ? 1024 / (MF_TILE * tile_tpr<S>()) : 1;
+}
+template <typename V, int S, bool FWD, bool CG, int TPR>
 __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restrict__ kk, const int* __restrict__ ff,
                                            const int64_t* __restrict__ rowoff, const int64_t* __restrict__ Moff,
                                            const V* __restrict__ M, const int* __restrict__ rows,
                                            const int64_t* __restrict__ cptr, const int* __restrict__ cidx,
                                            const int64_t* __restrict__ Doff, const V* __restrict__ Dinv, V* Xsub,
                                            V* Wout, V* P, int s, unsigned char* smem_raw) {
+  static_assert(S % TPR == 0, "columns split evenly over the threads of a row");
+  constexpr int CPT = S / TPR;  // columns per thread
   V(*bs)[S] = reinterpret_cast<V(*)[S]>(smem_raw);  // [MF_TK][S]
   const int t = tile.x, r0 = tile.y, c0 = tile.z, slot = tile.w;
   const int f = ff[t], k = kk[t];
@@ -151,8 +167,9 @@ __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restric
   const V* Mt = M + Moff[t];
   const int64_t ro = rowoff[t];
   const int tid = threadIdx.x;
+  const int row = tid / TPR, cb = (tid % TPR) * CPT;  // output row of the tile, first column
   const int lmax = max(0, kstop - kbeg);
-  const int rr = r0 + tid;
+  const int rr = r0 + row;
   const bool act = rr < nout;
   const V* mcol = Mt + (act ? rr : 0) + (int64_t)kbeg * ld;
   // the first factor columns are read while the input rows are staged
@@ -160,29 +177,30 @@ __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restric
 #pragma unroll
   for (int u = 0; u < MF_UNROLL; ++u)
     m0[u] = (act && u < lmax) ? __ldg(mcol + (int64_t)u * ld) : mk2((decltype(V::x))0, (decltype(V::x))0);
-  for (int l = tid; l < lmax; l += MF_TILE) {
+  for (int l = row; l < lmax; l += MF_TILE) {
     const int64_t R = ro + kbeg + l;
     const int local = kbeg + l;
-    V v[S];
+    V v[CPT];
     const V* src = (FWD || local >= k) ? Xsub + (int64_t)rows[R] * s : Wout + R * s;
 #pragma unroll
-    for (int c = 0; c < S; ++c) v[c] = c < s ? ldv<CG>(src + c) : mk2((decltype(V::x))0, (decltype(V::x))0);
+    for (int q = 0; q < CPT; ++q)
+      v[q] = cb + q < s ? ldv<CG>(src + cb + q) : mk2((decltype(V::x))0, (decltype(V::x))0);
     if (FWD) {
       const int64_t pe = cptr[R + 1];
       for (int64_t p = cptr[R]; p < pe; ++p) {
         const V* w = Wout + (int64_t)cidx[p] * s;
 #pragma unroll
-        for (int c = 0; c < S; ++c)
-          if (c < s) v[c] = c_add(v[c], ldv<CG>(w + c));
+        for (int q = 0; q < CPT; ++q)
+          if (cb + q < s) v[q] = c_add(v[q], ldv<CG>(w + cb + q));
       }
     }
 #pragma unroll
-    for (int c = 0; c < S; ++c) bs[l][c] = v[c];
+    for (int q = 0; q < CPT; ++q) bs[l][cb + q] = v[q];
   }
   __syncthreads();
-  V acc[S];
+  V acc[CPT];
 #pragma unroll
-  for (int c = 0; c < S; ++c) acc[c] = mk2((decltype(V::x))0, (decltype(V::x))0);
+  for (int q = 0; q < CPT; ++q) acc[q] = mk2((decltype(V::x))0, (decltype(V::x))0);
   if (act) {
     // software pipeline: the next MF_UNROLL factor columns are in flight while the current ones are used
     int j = 0;
@@ -196,17 +214,17 @@ __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restric
       for (int u = 0; u < MF_UNROLL; ++u)
         if (j + u < lmax)
 #pragma unroll
-          for (int c = 0; c < S; ++c) acc[c] = c_fma(m0[u], bs[j + u][c], acc[c]);
+          for (int q = 0; q < CPT; ++q) acc[q] = c_fma(m0[u], bs[j + u][cb + q], acc[q]);
 #pragma unroll
       for (int u = 0; u < MF_UNROLL; ++u) m0[u] = m1[u];
       j = jn;
     }
   }
   if (slot >= 0) {
-    V* out = P + ((int64_t)slot * MF_TILE + tid) * s;
+    V* out = P + ((int64_t)slot * MF_TILE + row) * s;
 #pragma unroll
-    for (int c = 0; c < S; ++c)
-      if (c < s) out[c] = acc[c];
+    for (int q = 0; q < CPT; ++q)
+      if (cb + q < s) out[cb + q] = acc[q];
     return;
   }
   if (!act) return;
@@ -215,8 +233,8 @@ __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restric
     if (rr < k) {
       const V di = Dinv[Doff[t] + rr];
 #pragma unroll
-      for (int c = 0; c < S; ++c)
-        if (c < s) Wout[Rg * s + c] = c_mul(acc[c], di);
+      for (int q = 0; q < CPT; ++q)
+        if (cb + q < s) Wout[Rg * s + cb + q] = c_mul(acc[q], di);
     } else {
       // parent update: the children's update vectors landing on this row,
       // one contiguous row of s values per contribution
@@ -224,23 +242,23 @@ __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restric
       for (int64_t p = cptr[Rg]; p < pe; ++p) {
         const V* w = Wout + (int64_t)cidx[p] * s;
 #pragma unroll
-        for (int c = 0; c < S; ++c)
-          if (c < s) acc[c] = c_add(acc[c], ldv<CG>(w + c));
+        for (int q = 0; q < CPT; ++q)
+          if (cb + q < s) acc[q] = c_add(acc[q], ldv<CG>(w + cb + q));
       }
 #pragma unroll
-      for (int c = 0; c < S; ++c)
-        if (c < s) Wout[Rg * s + c] = acc[c];
+      for (int q = 0; q < CPT; ++q)
+        if (cb + q < s) Wout[Rg * s + cb + q] = acc[q];
     }
   } else {
     V* xo = Xsub + (int64_t)rows[Rg] * s;
 #pragma unroll
-    for (int c = 0; c < S; ++c)
-      if (c < s) xo[c] = acc[c];
+    for (int q = 0; q < CPT; ++q)
+      if (cb + q < s) xo[cb + q] = acc[q];
   }
 }
 
 template <typename V, int S, bool FWD>
-__global__ void __launch_bounds__(MF_TILE) k_mf_tile(const int4* __restrict__ tiles, const int* __restrict__ kk,
+__global__ void __launch_bounds__(MF_TILE * tile_tpr<S>(), tile_min_blocks<V, S>()) k_mf_tile(const int4* __restrict__ tiles, const int* __restrict__ kk,
                                                      const int* __restrict__ ff, const int64_t* __restrict__ rowoff,
                                                      const int64_t* __restrict__ Moff, const V* __restrict__ M,
                                                      const int* __restrict__ rows, const int64_t* __restrict__ cptr,
@@ -248,7 +266,7 @@ __global__ void __launch_bounds__(MF_TILE) k_mf_tile(const int4* __restrict__ ti
                                                      const V* __restrict__ Dinv, V* __restrict__ Xsub,
                                                      V* __restrict__ Wout, V* __restrict__ P, int s) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  sweep_tile<V, S, FWD, false>(tiles[blockIdx.x], kk, ff, rowoff, Moff, M, rows, cptr, cidx, Doff, Dinv, Xsub, Wout,
+  sweep_tile<V, S, FWD, false, tile_tpr<S>()>(tiles[blockIdx.x], kk, ff, rowoff, Moff, M, rows, cptr, cidx, Doff, Dinv, Xsub, Wout,
                                P, s, smem_raw);
 }
 
@@ -377,7 +395,7 @@ __global__ void __launch_bounds__(MF_TILE) k_mf_sweep(
     const int tk = s_tile;
     if (tk >= ntiles) break;
     const int4 tile = tiles[tk];
-    sweep_tile<V, S, FWD, true>(tile, kk, ff, rowoff, Moff, M, rows, cptr, cidx, Doff, Dinv, Xsub, Wout, P, s,
+    sweep_tile<V, S, FWD, true, 1>(tile, kk, ff, rowoff, Moff, M, rows, cptr, cidx, Doff, Dinv, Xsub, Wout, P, s,
                                 smem_raw);
     __syncthreads();  // every write of the tile is issued
     const int g = tile.x;
@@ -857,7 +875,7 @@ static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
     const int tb = fptr[l], te = fptr[l + 1];
     cudaStream_t ss = fork_begin();
     if (te > tb)
-      { k_mf_tile<V, S, true><<<te - tb, MF_TILE, shm, ss>>>(ftl + tb, mf.k, mf.f, mf.rowoff, mf.Moff, M, mf.rows,
+      { k_mf_tile<V, S, true><<<te - tb, MF_TILE * tile_tpr<S>(), shm, ss>>>(ftl + tb, mf.k, mf.f, mf.rowoff, mf.Moff, M, mf.rows,
                                                              mf.cptr, mf.cidx, mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
     if (tc) tc_launch<V, S, true>(mf, l, Xsub, s, st);
     fork_end();
@@ -870,7 +888,7 @@ static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
     const int tb = bptr[l], te = bptr[l + 1];
     cudaStream_t ss = fork_begin();
     if (te > tb)
-      { k_mf_tile<V, S, false><<<te - tb, MF_TILE, shm, ss>>>(btl + tb, mf.k, mf.f, mf.rowoff, mf.Moff, MT,
+      { k_mf_tile<V, S, false><<<te - tb, MF_TILE * tile_tpr<S>(), shm, ss>>>(btl + tb, mf.k, mf.f, mf.rowoff, mf.Moff, MT,
                                                               mf.rows, mf.cptr, mf.cidx, mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
     if (tc) tc_launch<V, S, false>(mf, l, Xsub, s, st);
     fork_end();
