@@ -129,8 +129,9 @@ typedef struct hz_options {
                                double-float arithmetic: each double is carried as a pair of FP32 numbers
                                (about 48 significant bits; Dekker's TwoProduct and Knuth's TwoSum), which
                                GB300 issues 64 times faster than FP64 fused multiply-adds. Relative error of
-                               a row of m nonzeros about m 2^-48 of sum |a_ij x_j|; values must lie in the
-                               FP32 range. 0: native FP64. The FP64 form always uses native FP64 */
+                               a row of m nonzeros about m 2^-48 of sum |a_ij x_j|; magnitudes from about
+                               1e-31 to 1e38 keep that precision (smaller ones FP32 precision). 0: native
+                               FP64. The FP64 form always uses native FP64 */
 } hz_options;
 
 typedef struct hz_stats {

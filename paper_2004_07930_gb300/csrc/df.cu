@@ -12,8 +12,9 @@
 // of sum |a_ij x_j| (FP64: m * 2^-53), far below what the residual test of
 // FGMRES needs. All operations use the _rn intrinsics so that the compiler
 // cannot contract a product and a sum into one FMA (which would break the
-// error-free transformations). Values must lie in the FP32 range, as the
-// mixed form's FP32 local solves already require.
+// error-free transformations). Magnitudes from about 2^-103 (1e-31) to 2^128
+// keep the full precision; smaller ones are carried with FP32 precision, like
+// the mixed form's FP32 local solves.
 //
 // Layouts: a complex FP64 block [n][s] double2 becomes [n][s] float4
 // (re_hi, re_lo, im_hi, im_lo), 16 bytes per entry like the FP64 block; the

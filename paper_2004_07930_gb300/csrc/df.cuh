@@ -11,21 +11,22 @@ namespace hz {
 // that they issue integer instructions instead of FP64-pipe conversions.
 //
 // x -> (hi, lo): hi keeps the sign, exponent and leading 24 significant bits
-// of x (truncated), lo the remaining 29 bits rounded to 24, so that
+// of x (truncated); lo is the remaining 29 bits rounded to 23, built from its
+// bits as (1 + r) 2^(E-23) - 2^(E-23) (one exact FP32 subtraction), so that
 // |hi + lo - x| <= 2^-47 |x|. Zeros and FP64 subnormals give (0, 0); values
-// outside the FP32 normal range fall back to one rounding (lo = 0).
+// outside [2^-103, 2^128) fall back to one rounding (lo = 0).
 static __device__ __forceinline__ float2 df_split(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
   const int e = (int)((b >> 52) & 0x7FF);
   if (e == 0) return make_float2(__uint_as_float(sign), 0.f);
   const int fe = e - 1023 + 127;
-  if (fe <= 0 || fe >= 255) return make_float2(__double2float_rn(x), 0.f);
+  if (fe <= 23 || fe >= 255) return make_float2(__double2float_rn(x), 0.f);
   const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
   const float hi = __uint_as_float(sign | ((unsigned)fe << 23) | (unsigned)(m >> 29));
-  float lo = __uint2float_rn((unsigned)(m & 0x1FFFFFFFull));  // times 2^(e - 1075)
-  const int se = e - 1075 + 127;
-  lo = se >= 1 ? __fmul_rn(lo, __uint_as_float((unsigned)se << 23)) : ldexpf(lo, e - 1075);
+  const unsigned base = (unsigned)(fe - 23) << 23;                        // 2^(E-23) as FP32 bits
+  const unsigned r23 = (unsigned)(((m & 0x1FFFFFFFull) + 32ull) >> 6);      // rounded, may carry to 2^23
+  const float lo = __fsub_rn(__uint_as_float(base + r23), __uint_as_float(base));
   return make_float2(hi, sign ? -lo : lo);
 }
 

@@ -135,17 +135,21 @@ __device__ __forceinline__ V ldv(const V* p) {
 // leaves room for several CTAs per SM. A tile with slot >= 0 writes its
 // partial result to P; the others apply the epilogue.
 constexpr int MF_UNROLL = 8;
-// threads per output row for a block width S (the per-level launches); the
-// persistent sweep keeps one thread per row
+// threads per output row for a block width S in the short launches (a level
+// with fewer than MF_SHORT_LEVEL tiles, where one tile's latency bounds the
+// launch); levels with more tiles, and the persistent sweep, keep one thread
+// per row
 template <int S>
 __host__ __device__ constexpr int tile_tpr() {
   return S >= 16 ? 4 : (S >= 8 ? 2 : 1);
 }
+constexpr int MF_SHORT_LEVEL = 1536;
 // complex FP32 tiles of up to 16 columns: at least 1024 resident threads per SM
-// (64 registers per thread; wider blocks keep their accumulators unbounded)
-template <typename V, int S>
+// with several threads per row (64 registers per thread), 5 blocks of 128 with
+// one (102 registers)
+template <typename V, int S, int TPR>
 __host__ __device__ constexpr int tile_min_blocks() {
-  return (sizeof(V) == 8 && S <= 16) ? 1024 / (MF_TILE * tile_tpr<S>()) : 1;
+  return (sizeof(V) == 8 && S <= 16) ? (TPR > 1 ? 1024 / (MF_TILE * TPR) : 5) : 1;
 }
 template <typename V, int S, bool FWD, bool CG, int TPR>
 __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restrict__ kk, const int* __restrict__ ff,
@@ -257,8 +261,8 @@ __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restric
   }
 }
 
-template <typename V, int S, bool FWD>
-__global__ void __launch_bounds__(MF_TILE * tile_tpr<S>(), tile_min_blocks<V, S>()) k_mf_tile(const int4* __restrict__ tiles, const int* __restrict__ kk,
+template <typename V, int S, bool FWD, int TPR>
+__global__ void __launch_bounds__(MF_TILE * TPR, tile_min_blocks<V, S, TPR>()) k_mf_tile(const int4* __restrict__ tiles, const int* __restrict__ kk,
                                                      const int* __restrict__ ff, const int64_t* __restrict__ rowoff,
                                                      const int64_t* __restrict__ Moff, const V* __restrict__ M,
                                                      const int* __restrict__ rows, const int64_t* __restrict__ cptr,
@@ -266,7 +270,7 @@ __global__ void __launch_bounds__(MF_TILE * tile_tpr<S>(), tile_min_blocks<V, S>
                                                      const V* __restrict__ Dinv, V* __restrict__ Xsub,
                                                      V* __restrict__ Wout, V* __restrict__ P, int s) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  sweep_tile<V, S, FWD, false, tile_tpr<S>()>(tiles[blockIdx.x], kk, ff, rowoff, Moff, M, rows, cptr, cidx, Doff, Dinv, Xsub, Wout,
+  sweep_tile<V, S, FWD, false, TPR>(tiles[blockIdx.x], kk, ff, rowoff, Moff, M, rows, cptr, cidx, Doff, Dinv, Xsub, Wout,
                                P, s, smem_raw);
 }
 
@@ -837,6 +841,20 @@ static void sweep_persistent(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
         mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
 }
 
+// One level's SIMT tiles: several threads per output row when the level has
+// few tiles (latency-bound), one otherwise.
+template <typename V, int S, bool FWD>
+static void launch_tiles(int ntiles, size_t shm, cudaStream_t st, const int4* tiles, const DevMF& mf, const V* M,
+                         const V* Dv, V* Xsub, V* Wout, V* P, int s) {
+  constexpr int TPR = tile_tpr<S>();
+  if (TPR > 1 && ntiles < MF_SHORT_LEVEL)
+    { k_mf_tile<V, S, FWD, TPR><<<ntiles, MF_TILE * TPR, shm, st>>>(tiles, mf.k, mf.f, mf.rowoff, mf.Moff, M, mf.rows,
+                                                                    mf.cptr, mf.cidx, mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
+  else
+    { k_mf_tile<V, S, FWD, 1><<<ntiles, MF_TILE, shm, st>>>(tiles, mf.k, mf.f, mf.rowoff, mf.Moff, M, mf.rows, mf.cptr,
+                                                            mf.cidx, mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
+}
+
 template <typename V, int S>
 static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
   const size_t shm = tile_smem_bytes<V, S>();
@@ -875,8 +893,7 @@ static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
     const int tb = fptr[l], te = fptr[l + 1];
     cudaStream_t ss = fork_begin();
     if (te > tb)
-      { k_mf_tile<V, S, true><<<te - tb, MF_TILE * tile_tpr<S>(), shm, ss>>>(ftl + tb, mf.k, mf.f, mf.rowoff, mf.Moff, M, mf.rows,
-                                                             mf.cptr, mf.cidx, mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
+      launch_tiles<V, S, true>(te - tb, shm, ss, ftl + tb, mf, M, Dv, Xsub, Wout, P, s);
     if (tc) tc_launch<V, S, true>(mf, l, Xsub, s, st);
     fork_end();
     const int rb = mf.frb_ptr_h[l], re = mf.frb_ptr_h[l + 1];
@@ -888,8 +905,7 @@ static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
     const int tb = bptr[l], te = bptr[l + 1];
     cudaStream_t ss = fork_begin();
     if (te > tb)
-      { k_mf_tile<V, S, false><<<te - tb, MF_TILE * tile_tpr<S>(), shm, ss>>>(btl + tb, mf.k, mf.f, mf.rowoff, mf.Moff, MT,
-                                                              mf.rows, mf.cptr, mf.cidx, mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
+      launch_tiles<V, S, false>(te - tb, shm, ss, btl + tb, mf, MT, Dv, Xsub, Wout, P, s);
     if (tc) tc_launch<V, S, false>(mf, l, Xsub, s, st);
     fork_end();
     const int rb = mf.brb_ptr_h[l], re = mf.brb_ptr_h[l + 1];
@@ -904,8 +920,10 @@ static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
 template <typename V, int S>
 static void tile_attrs() {
   const int shm = (int)tile_smem_bytes<V, S>();
-  cudaFuncSetAttribute(k_mf_tile<V, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
-  cudaFuncSetAttribute(k_mf_tile<V, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+  cudaFuncSetAttribute(k_mf_tile<V, S, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+  cudaFuncSetAttribute(k_mf_tile<V, S, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+  cudaFuncSetAttribute(k_mf_tile<V, S, true, tile_tpr<S>()>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+  cudaFuncSetAttribute(k_mf_tile<V, S, false, tile_tpr<S>()>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
   cudaFuncSetAttribute(k_mf_sweep<V, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
   cudaFuncSetAttribute(k_mf_sweep<V, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
   {
