@@ -143,6 +143,9 @@ def parse():
     ap.add_argument("--serving-freqs", default="3.5,5,7")
     ap.add_argument("--serving-requests", type=int, default=400)
     ap.add_argument("--serving-rate", type=float, default=2.0, help="mean request arrivals per second")
+    ap.add_argument("--serving-loads", default="",
+                    help="comma-separated fractions of the measured saturation rate (e.g. 0.5,0.8,1.2): "
+                         "calibrate, then run the same seeded stream at each offered load")
     ap.add_argument("--serving-slots", type=int, default=32, help="right-hand-side slots per frequency "
                     "(when --serving-budget-gb is 0)")
     ap.add_argument("--serving-budget-gb", type=float, default=60.0,
@@ -495,14 +498,49 @@ def run_serving(args):
         sizes[f] = solvers[f].n
     rng = np.random.Generator(np.random.PCG64(7))
     N = args.serving_requests
-    arrival = np.cumsum(rng.exponential(1.0 / args.serving_rate, N))
+    gaps = rng.exponential(1.0, N)  # unit-rate gaps, scaled by the request rate below
     nsrc = rng.integers(1, 33, N)
     fsel = rng.integers(0, len(freqs), N)
-    reqs = []
+    srcs = []
     for i in range(N):
         xy = rng.uniform(1000.0, 19000.0, size=(nsrc[i], 2))
-        src = np.concatenate([xy, np.full((nsrc[i], 1), 100.0)], axis=1)
-        reqs.append((float(arrival[i]), i, freqs[fsel[i]], src))
+        srcs.append(np.concatenate([xy, np.full((nsrc[i], 1), 100.0)], axis=1))
+    loads = [float(x) for x in args.serving_loads.split(",") if x]
+    if loads:
+        # saturation: device time per right-hand side averaged over the frequency mix, from one
+        # timed block of 32 seeded sources per frequency
+        per_rhs = []
+        for f in freqs:
+            xy = rng.uniform(1000.0, 19000.0, size=(32, 2))
+            src = np.concatenate([xy, np.full((32, 1), 100.0)], axis=1)
+            solvers[f].solve(src[:4])
+            torch.cuda.synchronize()
+            t0 = time.time()
+            solvers[f].solve(src)
+            torch.cuda.synchronize()
+            per_rhs.append((time.time() - t0) / 32)
+        sat = 1.0 / float(np.mean(per_rhs))
+        mean_src = float(np.mean(nsrc))
+        for load in loads:
+            rate = load * sat / mean_src
+            arrival = np.cumsum(gaps / rate)
+            reqs = [(float(arrival[i]), i, freqs[fsel[i]], srcs[i]) for i in range(N)]
+            loop = ServingLoop(solvers, device_budget=args.serving_budget_gb * 1e9)
+            summ = loop.run_stream(reqs)
+            loop.close()
+            print(json.dumps({"mode": "serving_load", "offered_fraction_of_saturation": load,
+                              "saturation_rhs_per_s": sat, "offered_rhs_per_s": load * sat,
+                              "request_rate_per_s": rate, "rhs_per_s": summ["rhs_per_s"],
+                              "latency_p50_s": summ["latency_p50_s"], "latency_p99_s": summ["latency_p99_s"],
+                              "requests": summ["requests"], "rhs": summ["rhs"], "wall_s": summ["wall_s"],
+                              "converged": summ["converged"], "slots": summ.get("slots"),
+                              "freqs": freqs, "n": [sizes[f] for f in freqs],
+                              "setup_s": {str(f): setup[f] for f in freqs}}), flush=True)
+        for S in solvers.values():
+            S.close()
+        return
+    arrival = np.cumsum(gaps / args.serving_rate)
+    reqs = [(float(arrival[i]), i, freqs[fsel[i]], srcs[i]) for i in range(N)]
     if args.serving_budget_gb > 0:
         loop = ServingLoop(solvers, device_budget=args.serving_budget_gb * 1e9)
     else:

@@ -268,15 +268,34 @@ __global__ void k_sol_update(const V* __restrict__ Zk, int64_t vstride, const do
   X[g] = x;
 }
 
+// double-float Gram-Schmidt products (below)
+template <typename VB, typename VW>
+static void mdot_df(DevKrylov& K, const VB* Vb, int64_t vstride, int ni, const VW* W, double2* out,
+                    cudaStream_t st, const int* mask = nullptr);
+
 template <typename V>
 static void column_norms_t(const V* X, int64_t n, int s, double* out, DevKrylov& K, cudaStream_t st) {
+  if constexpr (std::is_same<V, double2>::value) {
+    if (K.df) {
+      mdot_df(K, X, 0, 1, X, K.h2, st);
+      { k_norm_finish<<<1, 64, 0, st>>>(K.h2, s, out); count_launch(); }
+      return;
+    }
+  }
   mdot<V>(K, X, 0, 1, X, K.h2, st);
   { k_norm_finish<<<1, 64, 0, st>>>(K.h2, s, out); count_launch(); }
 }
 
 template <typename V>
 static void krylov_start_t(DevKrylov& K, const V* R, cudaStream_t st) {
-  mdot<V>(K, R, 0, 1, R, K.h2, st);
+  if constexpr (std::is_same<V, double2>::value) {
+    if (K.df)
+      mdot_df(K, R, 0, 1, R, K.h2, st);
+    else
+      mdot<V>(K, R, 0, 1, R, K.h2, st);
+  } else {
+    mdot<V>(K, R, 0, 1, R, K.h2, st);
+  }
   { k_start<<<1, 64, 0, st>>>(K.s, K.m, K.h2, K.tol, K.g, K.beta, K.kc, K.done, K.res); count_launch(); }
   { k_scale_cols<V><<<grid_for(K.n * K.s, 256), 256, 0, st>>>(R, K.beta, (V*)K.V, K.n, K.s); count_launch(); }
 }
@@ -314,6 +333,8 @@ __device__ __forceinline__ float4 df_split2(const double2 v) {
   const float2 r = df_split(v.x), i = df_split(v.y);
   return make_float4(r.x, r.y, i.x, i.y);
 }
+__device__ __forceinline__ float4 as_df(const float4 v) { return v; }
+__device__ __forceinline__ float4 as_df(const double2 v) { return df_split2(v); }
 
 // (reh, rel, imh, iml) += conj(v) w
 __device__ __forceinline__ void df_conj_mac(float4& a, const float4 v, const float4 w) {
@@ -323,9 +344,10 @@ __device__ __forceinline__ void df_conj_mac(float4& a, const float4 v, const flo
   df_mac(a.z, a.w, -v.z, -v.w, w.x, w.y);  // im -= vi wr
 }
 
-template <typename VB>  // basis: double2 (FP64, split as read) or float4 (double-float)
+// VB, VW: double2 (FP64, split as read) or float4 (double-float)
+template <typename VB, typename VW>
 __global__ void k_mdot_df(const VB* __restrict__ Vb, int64_t vstride, int i0, int ni,
-                          const float4* __restrict__ W, int64_t n, int s, int64_t rows_per_blk,
+                          const VW* __restrict__ W, int64_t n, int s, int64_t rows_per_blk,
                           double2* __restrict__ part, int mstride, const int* __restrict__ mask) {
   __shared__ double2 sh[KBLOCK];
   const int nrl = blockDim.x / s;
@@ -336,16 +358,10 @@ __global__ void k_mdot_df(const VB* __restrict__ Vb, int64_t vstride, int i0, in
   const int64_t r0 = blockIdx.x * rows_per_blk;
   const int64_t r1 = (mask && !mask[c]) ? r0 : min(n, r0 + rows_per_blk);
   for (int64_t r = r0 + rl; r < r1; r += nrl) {
-    const float4 w = W[r * s + c];
+    const float4 w = as_df(W[r * s + c]);
 #pragma unroll
     for (int q = 0; q < IG; ++q)
-      if (q < ni) {
-        const VB vb = Vb[(int64_t)(i0 + q) * vstride + r * s + c];
-        if constexpr (std::is_same<VB, float4>::value)
-          df_conj_mac(acc[q], vb, w);
-        else
-          df_conj_mac(acc[q], df_split2(vb), w);
-      }
+      if (q < ni) df_conj_mac(acc[q], as_df(Vb[(int64_t)(i0 + q) * vstride + r * s + c]), w);
   }
   for (int q = 0; q < ni; ++q) {
     sh[threadIdx.x] = make_double2(f2d(acc[q].x) + f2d(acc[q].y), f2d(acc[q].z) + f2d(acc[q].w));
@@ -359,14 +375,14 @@ __global__ void k_mdot_df(const VB* __restrict__ Vb, int64_t vstride, int i0, in
   }
 }
 
-template <typename VB>
-static void mdot_df(DevKrylov& K, const VB* Vb, int64_t vstride, int ni, const float4* W, double2* out,
-                    cudaStream_t st, const int* mask = nullptr) {
+template <typename VB, typename VW>
+static void mdot_df(DevKrylov& K, const VB* Vb, int64_t vstride, int ni, const VW* W, double2* out,
+                    cudaStream_t st, const int* mask) {
   const int s = K.s;
   const int block = (KBLOCK / s) * s;
   const int64_t rpb = (K.n + K.nblk - 1) / K.nblk;
   for (int i0 = 0; i0 < ni; i0 += IG)
-    { k_mdot_df<VB><<<K.nblk, block, 0, st>>>(Vb, vstride, i0, std::min(IG, ni - i0), W, K.n, s, rpb, K.hpart,
+    { k_mdot_df<VB, VW><<<K.nblk, block, 0, st>>>(Vb, vstride, i0, std::min(IG, ni - i0), W, K.n, s, rpb, K.hpart,
                                             K.m + 1, mask); count_launch(); }
   { k_reduce_part<<<grid_for((int64_t)ni * s * 32, 256), 256, 0, st>>>(K.hpart, K.nblk, ni, s, K.m + 1, out); count_launch(); }
 }

@@ -151,6 +151,14 @@ template <typename V, int S, int TPR>
 __host__ __device__ constexpr int tile_min_blocks() {
   return (sizeof(V) == 8 && S <= 16) ? (TPR > 1 ? 1024 / (MF_TILE * TPR) : 5) : 1;
 }
+// Programmatic dependent launch (sm_90 and later): a kernel launched with
+// programmatic stream serialisation may start while its predecessor in the
+// stream is finishing; pdl_wait() blocks until the predecessor has completed
+// and its writes are visible, pdl_trigger() lets the successor be scheduled.
+// Both are no-ops for kernels launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <typename V, int S, bool FWD, bool CG, int TPR>
 __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restrict__ kk, const int* __restrict__ ff,
                                            const int64_t* __restrict__ rowoff, const int64_t* __restrict__ Moff,
@@ -181,6 +189,8 @@ __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restric
 #pragma unroll
   for (int u = 0; u < MF_UNROLL; ++u)
     m0[u] = (act && u < lmax) ? __ldg(mcol + (int64_t)u * ld) : mk2((decltype(V::x))0, (decltype(V::x))0);
+  // everything above reads set-up data only; the input rows come from the previous launches
+  pdl_wait();
   for (int l = row; l < lmax; l += MF_TILE) {
     const int64_t R = ro + kbeg + l;
     const int local = kbeg + l;
@@ -270,6 +280,7 @@ __global__ void __launch_bounds__(MF_TILE * TPR, tile_min_blocks<V, S, TPR>()) k
                                                      const V* __restrict__ Dinv, V* __restrict__ Xsub,
                                                      V* __restrict__ Wout, V* __restrict__ P, int s) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_trigger();
   sweep_tile<V, S, FWD, false, TPR>(tiles[blockIdx.x], kk, ff, rowoff, Moff, M, rows, cptr, cidx, Doff, Dinv, Xsub, Wout,
                                P, s, smem_raw);
 }
@@ -314,10 +325,12 @@ __global__ void k_mf_reduce(const int4* __restrict__ rblocks, int nrb, const int
                             const int64_t* __restrict__ cptr, const int* __restrict__ cidx,
                             const V* __restrict__ Dinv, V* __restrict__ Wout, const V* __restrict__ P,
                             V* __restrict__ Xsub, int s) {
+  pdl_trigger();
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t per = (int64_t)MF_TILE * s;
   if (g >= nrb * per) return;
   const int i = (int)((g % per) / s), c = (int)(g % s);
+  pdl_wait();
   rb_epilogue<V, FWD, false>(rblocks[g / per], i, c, kk, ff, rowoff, Doff, rows, cptr, cidx, Dinv, Wout, P, Xsub, s);
 }
 
@@ -841,18 +854,40 @@ static void sweep_persistent(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
         mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
 }
 
+// Launch with programmatic stream serialisation when `pdl` (the sweep's
+// tile and reduce launches: the next level's CTAs are scheduled while the
+// previous launch drains and read their factor columns before pdl_wait()).
+template <typename... P, typename... A>
+static void launch_k(bool pdl, void (*k)(P...), unsigned grid, unsigned block, size_t shm, cudaStream_t st,
+                     A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = shm;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+  count_launch();
+}
+
 // One level's SIMT tiles: several threads per output row when the level has
 // few tiles (latency-bound), one otherwise.
 template <typename V, int S, bool FWD>
-static void launch_tiles(int ntiles, size_t shm, cudaStream_t st, const int4* tiles, const DevMF& mf, const V* M,
-                         const V* Dv, V* Xsub, V* Wout, V* P, int s) {
+static void launch_tiles(bool pdl, int ntiles, size_t shm, cudaStream_t st, const int4* tiles, const DevMF& mf,
+                         const V* M, const V* Dv, V* Xsub, V* Wout, V* P, int s) {
   constexpr int TPR = tile_tpr<S>();
   if (TPR > 1 && ntiles < MF_SHORT_LEVEL)
-    { k_mf_tile<V, S, FWD, TPR><<<ntiles, MF_TILE * TPR, shm, st>>>(tiles, mf.k, mf.f, mf.rowoff, mf.Moff, M, mf.rows,
-                                                                    mf.cptr, mf.cidx, mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
+    launch_k(pdl, k_mf_tile<V, S, FWD, TPR>, ntiles, MF_TILE * TPR, shm, st, tiles, (const int*)mf.k,
+             (const int*)mf.f, (const int64_t*)mf.rowoff, (const int64_t*)mf.Moff, M, (const int*)mf.rows,
+             (const int64_t*)mf.cptr, (const int*)mf.cidx, (const int64_t*)mf.Doff, Dv, Xsub, Wout, P, s);
   else
-    { k_mf_tile<V, S, FWD, 1><<<ntiles, MF_TILE, shm, st>>>(tiles, mf.k, mf.f, mf.rowoff, mf.Moff, M, mf.rows, mf.cptr,
-                                                            mf.cidx, mf.Doff, Dv, Xsub, Wout, P, s); count_launch(); }
+    launch_k(pdl, k_mf_tile<V, S, FWD, 1>, ntiles, MF_TILE, shm, st, tiles, (const int*)mf.k, (const int*)mf.f,
+             (const int64_t*)mf.rowoff, (const int64_t*)mf.Moff, M, (const int*)mf.rows, (const int64_t*)mf.cptr,
+             (const int*)mf.cidx, (const int64_t*)mf.Doff, Dv, Xsub, Wout, P, s);
 }
 
 template <typename V, int S>
@@ -878,6 +913,8 @@ static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
   // tensor-core mode: a level's SIMT tiles run on the side stream, concurrently with its tcgen05 tiles
   // (they write disjoint outputs and partial slots); the level's reduce waits for both
   const bool fork = tc && mf.side;
+  // programmatic dependent launches between the levels (not with the tensor-core fork/join)
+  const bool pdl = !tc;
   auto fork_begin = [&]() {
     if (!fork) return st;
     cudaEventRecord(mf.ev_fork, st);
@@ -893,25 +930,29 @@ static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
     const int tb = fptr[l], te = fptr[l + 1];
     cudaStream_t ss = fork_begin();
     if (te > tb)
-      launch_tiles<V, S, true>(te - tb, shm, ss, ftl + tb, mf, M, Dv, Xsub, Wout, P, s);
+      launch_tiles<V, S, true>(pdl, te - tb, shm, ss, ftl + tb, mf, M, Dv, Xsub, Wout, P, s);
     if (tc) tc_launch<V, S, true>(mf, l, Xsub, s, st);
     fork_end();
     const int rb = mf.frb_ptr_h[l], re = mf.frb_ptr_h[l + 1];
     if (re > rb)
-      { k_mf_reduce<V, true><<<blocks_for((int64_t)(re - rb) * MF_TILE * s, 256), 256, 0, st>>>(
-          mf.frb + rb, re - rb, mf.k, mf.f, mf.rowoff, mf.Doff, mf.rows, mf.cptr, mf.cidx, Dv, Wout, P, Xsub, s); count_launch(); }
+      launch_k(pdl, k_mf_reduce<V, true>, blocks_for((int64_t)(re - rb) * MF_TILE * s, 256), 256, 0, st,
+               (const int4*)(mf.frb + rb), re - rb, (const int*)mf.k, (const int*)mf.f, (const int64_t*)mf.rowoff,
+               (const int64_t*)mf.Doff, (const int*)mf.rows, (const int64_t*)mf.cptr, (const int*)mf.cidx, Dv, Wout,
+               (const V*)P, Xsub, s);
   }
   for (int l = mf.nlevels - 1; l >= 0; --l) {
     const int tb = bptr[l], te = bptr[l + 1];
     cudaStream_t ss = fork_begin();
     if (te > tb)
-      launch_tiles<V, S, false>(te - tb, shm, ss, btl + tb, mf, MT, Dv, Xsub, Wout, P, s);
+      launch_tiles<V, S, false>(pdl, te - tb, shm, ss, btl + tb, mf, MT, Dv, Xsub, Wout, P, s);
     if (tc) tc_launch<V, S, false>(mf, l, Xsub, s, st);
     fork_end();
     const int rb = mf.brb_ptr_h[l], re = mf.brb_ptr_h[l + 1];
     if (re > rb)
-      { k_mf_reduce<V, false><<<blocks_for((int64_t)(re - rb) * MF_TILE * s, 256), 256, 0, st>>>(
-          mf.brb + rb, re - rb, mf.k, mf.f, mf.rowoff, mf.Doff, mf.rows, mf.cptr, mf.cidx, Dv, Wout, P, Xsub, s); count_launch(); }
+      launch_k(pdl, k_mf_reduce<V, false>, blocks_for((int64_t)(re - rb) * MF_TILE * s, 256), 256, 0, st,
+               (const int4*)(mf.brb + rb), re - rb, (const int*)mf.k, (const int*)mf.f, (const int64_t*)mf.rowoff,
+               (const int64_t*)mf.Doff, (const int*)mf.rows, (const int64_t*)mf.cptr, (const int*)mf.cidx, Dv, Wout,
+               (const V*)P, Xsub, s);
   }
 }
 
