@@ -132,6 +132,8 @@ def parse():
     ap.add_argument("--persistent", type=int, choices=[-1, 0, 1], default=-1,
                     help="SIMT front sweeps as one launch per direction (1) or one per level (0); -1: library default")
     ap.add_argument("--leaf-size", type=int, default=0, help="nested-dissection leaf size (0: library default)")
+    ap.add_argument("--coarse-leaf-size", type=int, default=-1,
+                    help="leaf size of the coarse level's local problems (-1: library default)")
     ap.add_argument("--emulate-fp64", type=int, choices=[-1, 0, 1], default=-1,
                     help="mixed form: FP64 products and Arnoldi as FP32 pairs (1) or native FP64 (0); -1: default")
     ap.add_argument("--spmm-sweep", action="store_true",
@@ -365,6 +367,8 @@ def measure_form(prob, form, steps, warmup, stream, ws, torch, hz, with_e2e, ser
         opts["emulate_fp64"] = EMULATE
     if LEAF > 0:
         opts["leaf_size"] = LEAF
+    if CLEAF >= 0:
+        opts["coarse_leaf_size"] = CLEAF
     if MAX_BLOCK > 0:
         opts["max_block"] = MAX_BLOCK
     t0 = time.time()
@@ -434,6 +438,7 @@ TENSOR_CORES = -1
 PERSISTENT = -1
 EMULATE = -1
 LEAF = 0
+CLEAF = -1
 MAX_BLOCK = 0
 
 
@@ -638,7 +643,7 @@ def run_scale(args):
 
 
 def main():
-    global MAXIT, TENSOR_CORES, PERSISTENT, MAX_BLOCK, EMULATE, LEAF
+    global MAXIT, TENSOR_CORES, PERSISTENT, MAX_BLOCK, EMULATE, LEAF, CLEAF
     args = parse()
     MAX_BLOCK = args.max_block
     MAXIT = args.maxit
@@ -646,6 +651,7 @@ def main():
     PERSISTENT = args.persistent
     EMULATE = args.emulate_fp64
     LEAF = args.leaf_size
+    CLEAF = args.coarse_leaf_size
     if args.impl == "reference":
         run_reference(args)
         return

@@ -132,6 +132,9 @@ typedef struct hz_options {
                                a row of m nonzeros about m 2^-48 of sum |a_ij x_j|; magnitudes from about
                                1e-31 to 1e38 keep that precision (smaller ones FP32 precision). 0: native
                                FP64. The FP64 form always uses native FP64 */
+  int32_t coarse_leaf_size; /* nested-dissection leaf size of the coarse level's local problems; 0 (default):
+                               the same as leaf_size. The coarse problems are small and their sweeps bound
+                               by per-level latency, so fewer, larger leaves can pay there */
 } hz_options;
 
 typedef struct hz_stats {

@@ -1516,6 +1516,7 @@ int hz_default_options(hz_options* o) {
   o->factor_fp32 = 1;
   o->recycle = 0;
   o->emulate_fp64 = 1;
+  o->coarse_leaf_size = 0;
   return HZ_OK;
 }
 
@@ -1542,6 +1543,7 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
     if (o.overlap < 1 || o.overlap > 16) throw HzError{HZ_EINVAL, "overlap must be in [1, 16]"};
     if (o.block_arnoldi != 0 && (o.block_arnoldi != 1 || o.max_block > 32))
       throw HzError{HZ_EINVAL, "block_arnoldi needs max_block <= 32"};
+    if (o.coarse_leaf_size < 0) throw HzError{HZ_EINVAL, "coarse_leaf_size < 0"};
     if (o.recycle < 0 || o.recycle > 16 || (o.recycle > 0 && (o.block_arnoldi || o.restart < 2)))
       throw HzError{HZ_EINVAL, "recycle must be in [0, 16], with per-column FGMRES and restart >= 2"};
     mesh_from_abi(fine, c->fine);
@@ -1597,9 +1599,11 @@ int hz_setup(const hz_mesh* fine, const double* velocity, double freq_hz, const 
       if (o.coarse_mode == HZ_COARSE_GMRES) {
         std::vector<Subdomain> csubs =
             build_subdomains(c->coarse, c->cspace, C.part, nparts, C.mvals, omega, o.overlap);
-        build_level(c->cspace, csubs, o.leaf_size, mixed, false, tc, pers, c->lc, c->pool, c->st);
+        build_level(c->cspace, csubs, o.coarse_leaf_size > 0 ? o.coarse_leaf_size : o.leaf_size, mixed, false, tc,
+                    pers, c->lc, c->pool, c->st);
       } else {
-        build_direct(c->cspace, C.E, o.leaf_size, mixed, tc, pers, c->lc, c->pool, c->st);
+        build_direct(c->cspace, C.E, o.coarse_leaf_size > 0 ? o.coarse_leaf_size : o.leaf_size, mixed, tc, pers,
+                     c->lc, c->pool, c->st);
       }
     }
     CK(cudaStreamSynchronize(c->st));

@@ -38,7 +38,7 @@ class HzOptions(C.Structure):
                 ("use_graphs", C.c_int32), ("tensor_cores", C.c_int32), ("overlap", C.c_int32),
                 ("coarse_fp32", C.c_int32), ("debug_bounds", C.c_int32), ("block_arnoldi", C.c_int32),
                 ("persistent_sweeps", C.c_int32), ("factor_fp32", C.c_int32),
-                ("recycle", C.c_int32), ("emulate_fp64", C.c_int32)]
+                ("recycle", C.c_int32), ("emulate_fp64", C.c_int32), ("coarse_leaf_size", C.c_int32)]
 
 
 class HzStats(C.Structure):

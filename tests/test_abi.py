@@ -38,7 +38,7 @@ def test_default_options(lib):
     assert o.rtol == 1e-6 and o.restart == 30 and o.max_block == 64 and o.coarse_inner_its == 10
     assert o.coarse_mode == hz.HZ_COARSE_GMRES
     assert o.overlap == 1 and o.coarse_fp32 == 0 and o.debug_bounds == 0 and o.tensor_cores == 0
-    assert o.recycle == 0
+    assert o.recycle == 0 and o.emulate_fp64 == 1
 
 
 def _setup_rc(prob, part=None, nparts=None, vel=None, freq=None, **opts):
