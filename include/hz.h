@@ -125,8 +125,11 @@ typedef struct hz_options {
                                (I - C C^H) A M^{-1}. 0 (default): off. Needs per-column FGMRES (block_arnoldi 0)
                                and restart >= 2; servers do not recycle. Costs 6 k n complex FP64 of device memory */
   int32_t emulate_fp64;     /* mixed form only. 1 (default): the products with A (Krylov products, true
-                               residuals, hz_apply_A) and, with the FP64 coarse level, with E run in
-                               double-float arithmetic: each double is carried as a pair of FP32 numbers
+                               residuals, hz_apply_A), the Gram-Schmidt products, updates and norms of the
+                               FGMRES iteration and, with the FP64 coarse level, the products with E, Z and
+                               Z^T and the coarse Krylov iteration run in double-float arithmetic (the
+                               Hessenberg matrix, rotations, least squares and solution update stay FP64):
+                               each double is carried as a pair of FP32 numbers
                                (about 48 significant bits; Dekker's TwoProduct and Knuth's TwoSum), which
                                GB300 issues 64 times faster than FP64 fused multiply-adds. Relative error of
                                a row of m nonzeros about m 2^-48 of sum |a_ij x_j|; magnitudes from about
