@@ -98,6 +98,8 @@ struct MFHost {
   std::vector<int64_t> level_row;
   // per-level algorithmic work of one solve sweep (complex multiply-adds per column)
   std::vector<double> fwd_cmacs, bwd_cmacs;
+  // per level: every tile has at most 64 output rows (half-height tiles in the solve)
+  std::vector<char> fhalf, bhalf;
 };
 
 // Pack the fronts of several local matrices into one device structure;
@@ -274,6 +276,8 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
     }
   };
   info.fwd_cmacs.assign(maxh + 1, 0.0);
+  info.fhalf.assign(maxh + 1, 1);
+  info.bhalf.assign(maxh + 1, 1);
   info.bwd_cmacs.assign(maxh + 1, 0.0);
   int64_t max_slots = 1;
   for (int l = 0; l <= maxh; ++l) {
@@ -285,6 +289,7 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
       // without pivots (k = 0) still passes its children's updates on: its
       // row blocks get one tile with an empty reduction
       for (int r0 = 0; r0 < f[g]; r0 += MF_TILE_ROWS) {
+        if (f[g] - r0 > 64) info.fhalf[l] = 0;
         const int kend = r0 < k[g] ? std::min(k[g], r0 + MF_TILE_ROWS) : k[g];
         const int nk = (kend + MF_TILE_K - 1) / MF_TILE_K;
         if (nk <= 1) {
@@ -299,6 +304,7 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
         }
       }
       for (int j0 = 0; j0 < k[g]; j0 += MF_TILE_ROWS) {
+        if (k[g] - j0 > 64) info.bhalf[l] = 0;
         const int nk = (f[g] - j0 + MF_TILE_K - 1) / MF_TILE_K;
         if (nk == 1) {
           btiles.push_back(make_int4(g, j0, j0, -1));
@@ -339,6 +345,8 @@ void build_mf(const std::vector<const CsrC*>& mats, const std::vector<const Fron
   mf.amap_total = (int64_t)amap_pos.size();
   mf.level_ptr_h = info.level_ptr.data();
   mf.ftile_ptr_h = info.ftile_ptr.data();
+  mf.fhalf_h = info.fhalf.data();
+  mf.bhalf_h = info.bhalf.data();
   mf.btile_ptr_h = info.btile_ptr.data();
   mf.frb_ptr_h = info.frb_ptr.data();
   mf.brb_ptr_h = info.brb_ptr.data();

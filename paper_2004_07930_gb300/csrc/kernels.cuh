@@ -39,6 +39,8 @@ struct DevMF {
   int fp32 = 0;
   int* level_ptr_h = nullptr;   // host [nlevels+1]
   int* ftile_ptr_h = nullptr;   // host [nlevels+1] forward tiles per level
+  const char* fhalf_h = nullptr;  // host [nlevels]: every forward tile of the level has <= 64 output rows
+  const char* bhalf_h = nullptr;  // host [nlevels]: the same for the backward tiles
   int* btile_ptr_h = nullptr;   // host [nlevels+1] backward tiles per level
   int* level_list = nullptr;    // device [nfronts] front ids ordered by height
   int* frb_ptr_h = nullptr;     // host [nlevels+1] forward row blocks per level

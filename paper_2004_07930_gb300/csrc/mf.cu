@@ -144,12 +144,20 @@ __host__ __device__ constexpr int tile_tpr() {
   return S >= 16 ? 4 : (S >= 8 ? 2 : 1);
 }
 constexpr int MF_SHORT_LEVEL = 1536;
-// complex FP32 tiles of up to 16 columns: at least 1024 resident threads per SM
-// with several threads per row (64 registers per thread), 5 blocks of 128 with
-// one (102 registers)
-template <typename V, int S, int TPR>
+// a long level whose tiles all have at most MF_HALF output rows (the leaf
+// fronts' pivot rows in the backward sweep, for instance) runs half-height
+// tiles: MF_HALF rows, tile_tpr_half threads per row, no idle threads
+constexpr int MF_HALF = 64;
+template <int S>
+__host__ __device__ constexpr int tile_tpr_half() {
+  return S >= 2 ? 2 : 1;
+}
+// complex FP32 tiles of up to 16 columns: 1024 resident threads per SM with
+// several threads per row (64 registers per thread), 6 half-height tiles of
+// 128 threads (85 registers), 5 blocks of 128 with one thread per row (102)
+template <typename V, int S, int TPR, int ROWS>
 __host__ __device__ constexpr int tile_min_blocks() {
-  return (sizeof(V) == 8 && S <= 16) ? (TPR > 1 ? 1024 / (MF_TILE * TPR) : 5) : 1;
+  return (sizeof(V) == 8 && S <= 16) ? (ROWS < MF_TILE ? 6 : (TPR > 1 ? 1024 / (MF_TILE * TPR) : 5)) : 1;
 }
 // Programmatic dependent launch (sm_90 and later): a kernel launched with
 // programmatic stream serialisation may start while its predecessor in the
@@ -159,7 +167,7 @@ __host__ __device__ constexpr int tile_min_blocks() {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-template <typename V, int S, bool FWD, bool CG, int TPR>
+template <typename V, int S, bool FWD, bool CG, int TPR, int ROWS>
 __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restrict__ kk, const int* __restrict__ ff,
                                            const int64_t* __restrict__ rowoff, const int64_t* __restrict__ Moff,
                                            const V* __restrict__ M, const int* __restrict__ rows,
@@ -167,6 +175,7 @@ __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restric
                                            const int64_t* __restrict__ Doff, const V* __restrict__ Dinv, V* Xsub,
                                            V* Wout, V* P, int s, unsigned char* smem_raw) {
   static_assert(S % TPR == 0, "columns split evenly over the threads of a row");
+  static_assert(ROWS <= MF_TILE, "a tile computes at most MF_TILE output rows");
   constexpr int CPT = S / TPR;  // columns per thread
   V(*bs)[S] = reinterpret_cast<V(*)[S]>(smem_raw);  // [MF_TK][S]
   const int t = tile.x, r0 = tile.y, c0 = tile.z, slot = tile.w;
@@ -191,7 +200,7 @@ __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restric
     m0[u] = (act && u < lmax) ? __ldg(mcol + (int64_t)u * ld) : mk2((decltype(V::x))0, (decltype(V::x))0);
   // everything above reads set-up data only; the input rows come from the previous launches
   pdl_wait();
-  for (int l = row; l < lmax; l += MF_TILE) {
+  for (int l = row; l < lmax; l += ROWS) {
     const int64_t R = ro + kbeg + l;
     const int local = kbeg + l;
     V v[CPT];
@@ -271,8 +280,8 @@ __device__ __forceinline__ void sweep_tile(const int4 tile, const int* __restric
   }
 }
 
-template <typename V, int S, bool FWD, int TPR>
-__global__ void __launch_bounds__(MF_TILE * TPR, tile_min_blocks<V, S, TPR>()) k_mf_tile(const int4* __restrict__ tiles, const int* __restrict__ kk,
+template <typename V, int S, bool FWD, int TPR, int ROWS>
+__global__ void __launch_bounds__(ROWS * TPR, tile_min_blocks<V, S, TPR, ROWS>()) k_mf_tile(const int4* __restrict__ tiles, const int* __restrict__ kk,
                                                      const int* __restrict__ ff, const int64_t* __restrict__ rowoff,
                                                      const int64_t* __restrict__ Moff, const V* __restrict__ M,
                                                      const int* __restrict__ rows, const int64_t* __restrict__ cptr,
@@ -281,7 +290,7 @@ __global__ void __launch_bounds__(MF_TILE * TPR, tile_min_blocks<V, S, TPR>()) k
                                                      V* __restrict__ Wout, V* __restrict__ P, int s) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_trigger();
-  sweep_tile<V, S, FWD, false, TPR>(tiles[blockIdx.x], kk, ff, rowoff, Moff, M, rows, cptr, cidx, Doff, Dinv, Xsub, Wout,
+  sweep_tile<V, S, FWD, false, TPR, ROWS>(tiles[blockIdx.x], kk, ff, rowoff, Moff, M, rows, cptr, cidx, Doff, Dinv, Xsub, Wout,
                                P, s, smem_raw);
 }
 
@@ -412,7 +421,7 @@ __global__ void __launch_bounds__(MF_TILE) k_mf_sweep(
     const int tk = s_tile;
     if (tk >= ntiles) break;
     const int4 tile = tiles[tk];
-    sweep_tile<V, S, FWD, true, 1>(tile, kk, ff, rowoff, Moff, M, rows, cptr, cidx, Doff, Dinv, Xsub, Wout, P, s,
+    sweep_tile<V, S, FWD, true, 1, MF_TILE>(tile, kk, ff, rowoff, Moff, M, rows, cptr, cidx, Doff, Dinv, Xsub, Wout, P, s,
                                 smem_raw);
     __syncthreads();  // every write of the tile is issued
     const int g = tile.x;
@@ -875,17 +884,23 @@ static void launch_k(bool pdl, void (*k)(P...), unsigned grid, unsigned block, s
 }
 
 // One level's SIMT tiles: several threads per output row when the level has
-// few tiles (latency-bound), one otherwise.
+// few tiles (latency-bound); on long levels half-height tiles when every tile
+// has at most MF_HALF output rows, else one thread per row.
 template <typename V, int S, bool FWD>
-static void launch_tiles(bool pdl, int ntiles, size_t shm, cudaStream_t st, const int4* tiles, const DevMF& mf,
-                         const V* M, const V* Dv, V* Xsub, V* Wout, V* P, int s) {
+static void launch_tiles(bool pdl, int ntiles, bool half, size_t shm, cudaStream_t st, const int4* tiles,
+                         const DevMF& mf, const V* M, const V* Dv, V* Xsub, V* Wout, V* P, int s) {
   constexpr int TPR = tile_tpr<S>();
-  if (TPR > 1 && ntiles < MF_SHORT_LEVEL)
-    launch_k(pdl, k_mf_tile<V, S, FWD, TPR>, ntiles, MF_TILE * TPR, shm, st, tiles, (const int*)mf.k,
+  constexpr int TPH = tile_tpr_half<S>();
+  if (half && ntiles >= MF_SHORT_LEVEL)
+    launch_k(pdl, k_mf_tile<V, S, FWD, TPH, MF_HALF>, ntiles, MF_HALF * TPH, shm, st, tiles, (const int*)mf.k,
+             (const int*)mf.f, (const int64_t*)mf.rowoff, (const int64_t*)mf.Moff, M, (const int*)mf.rows,
+             (const int64_t*)mf.cptr, (const int*)mf.cidx, (const int64_t*)mf.Doff, Dv, Xsub, Wout, P, s);
+  else if (TPR > 1 && ntiles < MF_SHORT_LEVEL)
+    launch_k(pdl, k_mf_tile<V, S, FWD, TPR, MF_TILE>, ntiles, MF_TILE * TPR, shm, st, tiles, (const int*)mf.k,
              (const int*)mf.f, (const int64_t*)mf.rowoff, (const int64_t*)mf.Moff, M, (const int*)mf.rows,
              (const int64_t*)mf.cptr, (const int*)mf.cidx, (const int64_t*)mf.Doff, Dv, Xsub, Wout, P, s);
   else
-    launch_k(pdl, k_mf_tile<V, S, FWD, 1>, ntiles, MF_TILE, shm, st, tiles, (const int*)mf.k, (const int*)mf.f,
+    launch_k(pdl, k_mf_tile<V, S, FWD, 1, MF_TILE>, ntiles, MF_TILE, shm, st, tiles, (const int*)mf.k, (const int*)mf.f,
              (const int64_t*)mf.rowoff, (const int64_t*)mf.Moff, M, (const int*)mf.rows, (const int64_t*)mf.cptr,
              (const int*)mf.cidx, (const int64_t*)mf.Doff, Dv, Xsub, Wout, P, s);
 }
@@ -930,7 +945,7 @@ static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
     const int tb = fptr[l], te = fptr[l + 1];
     cudaStream_t ss = fork_begin();
     if (te > tb)
-      launch_tiles<V, S, true>(pdl, te - tb, shm, ss, ftl + tb, mf, M, Dv, Xsub, Wout, P, s);
+      launch_tiles<V, S, true>(pdl, te - tb, mf.fhalf_h[l] != 0, shm, ss, ftl + tb, mf, M, Dv, Xsub, Wout, P, s);
     if (tc) tc_launch<V, S, true>(mf, l, Xsub, s, st);
     fork_end();
     const int rb = mf.frb_ptr_h[l], re = mf.frb_ptr_h[l + 1];
@@ -944,7 +959,7 @@ static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
     const int tb = bptr[l], te = bptr[l + 1];
     cudaStream_t ss = fork_begin();
     if (te > tb)
-      launch_tiles<V, S, false>(pdl, te - tb, shm, ss, btl + tb, mf, MT, Dv, Xsub, Wout, P, s);
+      launch_tiles<V, S, false>(pdl, te - tb, mf.bhalf_h[l] != 0, shm, ss, btl + tb, mf, MT, Dv, Xsub, Wout, P, s);
     if (tc) tc_launch<V, S, false>(mf, l, Xsub, s, st);
     fork_end();
     const int rb = mf.brb_ptr_h[l], re = mf.brb_ptr_h[l + 1];
@@ -961,10 +976,14 @@ static void solve_impl(DevMF& mf, V* Xsub, int s, cudaStream_t st) {
 template <typename V, int S>
 static void tile_attrs() {
   const int shm = (int)tile_smem_bytes<V, S>();
-  cudaFuncSetAttribute(k_mf_tile<V, S, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
-  cudaFuncSetAttribute(k_mf_tile<V, S, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
-  cudaFuncSetAttribute(k_mf_tile<V, S, true, tile_tpr<S>()>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
-  cudaFuncSetAttribute(k_mf_tile<V, S, false, tile_tpr<S>()>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+  cudaFuncSetAttribute(k_mf_tile<V, S, true, 1, MF_TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+  cudaFuncSetAttribute(k_mf_tile<V, S, false, 1, MF_TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+  cudaFuncSetAttribute(k_mf_tile<V, S, true, tile_tpr<S>(), MF_TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+  cudaFuncSetAttribute(k_mf_tile<V, S, false, tile_tpr<S>(), MF_TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+  cudaFuncSetAttribute(k_mf_tile<V, S, true, tile_tpr_half<S>(), MF_HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       shm);
+  cudaFuncSetAttribute(k_mf_tile<V, S, false, tile_tpr_half<S>(), MF_HALF>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
   cudaFuncSetAttribute(k_mf_sweep<V, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
   cudaFuncSetAttribute(k_mf_sweep<V, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
   {
