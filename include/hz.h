@@ -99,7 +99,8 @@ typedef struct hz_options {
   int32_t overlap;          /* element layers added around each subdomain, each layer = every element
                                sharing a vertex with the current set (1, the default; >= 1) */
   int32_t coarse_fp32;      /* mixed form only. 0 (default): E = Z^T A Z, Z, Z^T and the inner coarse GMRES
-                               run in FP64; the coarse fronts, factorised in FP64 like all fronts, are applied
+                               run with FP64 accuracy (as FP32 pairs under emulate_fp64); the coarse fronts,
+                               factorised in FP64 like all fronts, are applied
                                in complex FP32 like the fine ones. 1: the whole of M^{-1}, coarse level
                                included, runs on complex FP32 blocks */
   int32_t debug_bounds;     /* 1: after the factorisation, one device pass checks every index map of the
@@ -133,8 +134,9 @@ typedef struct hz_options {
                                (about 48 significant bits; Dekker's TwoProduct and Knuth's TwoSum), which
                                GB300 issues 64 times faster than FP64 fused multiply-adds. Relative error of
                                a row of m nonzeros about m 2^-48 of sum |a_ij x_j|; magnitudes from about
-                               1e-31 to 1e38 keep that precision (smaller ones FP32 precision). 0: native
-                               FP64. The FP64 form always uses native FP64 */
+                               1e-31 to 1e38 keep that precision (smaller ones FP32 precision). With
+                               block_arnoldi or recycle the outer Krylov iteration (not its products) stays in
+                               native FP64. 0: native FP64. The FP64 form always uses native FP64 */
   int32_t coarse_leaf_size; /* nested-dissection leaf size of the coarse level's local problems; 0 (default):
                                the same as leaf_size. The coarse problems are small and their sweeps bound
                                by per-level latency, so fewer, larger leaves can pay there */
