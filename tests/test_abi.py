@@ -39,6 +39,10 @@ def test_default_options(lib):
     assert o.coarse_mode == hz.HZ_COARSE_GMRES
     assert o.overlap == 1 and o.coarse_fp32 == 0 and o.debug_bounds == 0 and o.tensor_cores == 0
     assert o.recycle == 0 and o.emulate_fp64 == 1
+    # every default the header documents
+    assert o.precision == hz.HZ_PREC_FP64 and o.maxit == 500 and o.leaf_size == 64 and o.pivot_tau == 1e-12
+    assert o.use_graphs == 1 and o.block_arnoldi == 0 and o.persistent_sweeps == 0 and o.factor_fp32 == 1
+    assert o.coarse_leaf_size == 0 and o.verbose == 0
 
 
 def _setup_rc(prob, part=None, nparts=None, vel=None, freq=None, **opts):
@@ -73,6 +77,7 @@ def test_setup_rejects_bad_inputs(lib):
     assert _setup_rc(p, recycle=-1) == hz.HZ_EINVAL
     assert _setup_rc(p, recycle=4, block_arnoldi=1, max_block=16) == hz.HZ_EINVAL  # per-column FGMRES only
     assert _setup_rc(p, recycle=4, restart=1) == hz.HZ_EINVAL
+    assert _setup_rc(p, coarse_leaf_size=-1) == hz.HZ_EINVAL
     assert "partition" in hz.load().hz_last_error().decode() or True
     assert lib.hz_strerror(hz.HZ_ENOTCONV).decode() == "not converged"
 
